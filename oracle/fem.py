@@ -242,3 +242,43 @@ def type_mask(mesh: Mesh, ts) -> np.ndarray:
         o = mesh.offsets[t]
         m[o:o + int(np.prod(mesh.shapes[t]))] = True
     return m
+
+
+def apply_rows(mesh: Mesh, prm: Params, kinv_L: np.ndarray, kinv_U: np.ndarray, x: np.ndarray,
+               rows) -> np.ndarray:
+    """(A x)[rows] computed one row at a time by summing the element contributions of the
+    triangles that hold each row's DoF (for sampled checks on grids too large to assemble).
+    Constrained rows return 0 and constrained entries of x are ignored."""
+    n = mesh.n
+    tris = reference_triangles(n)
+    parts = {o: element_parts(tris[o]) for o in ("L", "U")}
+    base = {o: element_matrix(parts[o], prm, 0.0) for o in ("L", "U")}
+    xf = np.where(mesh.free, x, 0.0)
+    out = np.zeros(len(rows))
+    for k, r in enumerate(rows):
+        if not mesh.free[r]:
+            continue
+        t = None
+        for tt in TYPES_ALL:
+            o_ = mesh.offsets[tt]
+            rr, cc = mesh.shapes[tt]
+            if o_ <= r < o_ + rr * cc:
+                t = tt
+                j, i = divmod(r - o_, cc)
+        acc = 0.0
+        for cj in range(max(0, j - 1), min(n, j + 1)):
+            for ci in range(max(0, i - 1), min(n, i + 1)):
+                for o in ("L", "U"):
+                    dofs = mesh.tri_dofs(o, ci, cj)
+                    hit = np.nonzero(dofs == r)[0]
+                    if hit.size == 0:
+                        continue
+                    E = base[o].copy()
+                    kin = (kinv_L if o == "L" else kinv_U)[cj, ci]
+                    E[9:12, 9:12] += prm.tau * kin * parts[o]["Mw"]
+                    acc += float(E[hit[0]] @ xf[dofs])
+        out[k] = acc
+    return out
+
+
+TYPES_ALL = ("ux", "uy", "bh", "bv", "bd", "wh", "wv", "wd", "pL", "pU")

@@ -32,6 +32,7 @@ class Mesh:
     def __init__(self, n: int, w_essential: bool = False):
         assert n >= 1
         self.n = n
+        self.w_essential = bool(w_essential)
         self.h = 1.0 / n
         self.shapes = synthetic.shapes(n)
         self.offsets = {}

@@ -54,12 +54,12 @@ class Vanka:
         self.groups = []
         for s, plist in groups.items():
             idx = np.array(plist, dtype=np.int64)                     # (G, s)
-            mats = np.empty((len(plist), s, s))
-            for g, p in enumerate(plist):
-                loc = A[p][:, p].toarray()
-                if p_shift != 0.0:
-                    loc[np.diag_indices(s)] += p_shift * pmask[p]
-                mats[g] = loc
+            # V_l A V_l^T for every patch of this size: entries A[idx[g, a], idx[g, b]]
+            rows = np.repeat(idx[:, :, None], s, axis=2)
+            cols = np.repeat(idx[:, None, :], s, axis=1)
+            mats = np.asarray(A[rows.ravel(), cols.ravel()]).reshape(len(plist), s, s)
+            if p_shift != 0.0:
+                mats[:, np.arange(s), np.arange(s)] += p_shift * pmask[idx]
             inv = np.linalg.inv(mats)
             self.groups.append((idx, inv))
 

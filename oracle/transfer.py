@@ -58,8 +58,19 @@ def _tri_object(verts, h):
     return Triangle(X, fams)
 
 
+_CACHE = {}
+
+
 def prolongation(fine: Mesh, coarse: Mesh) -> sp.csr_matrix:
-    """P: coarse vector -> fine vector, rows/columns of constrained DoFs removed (zeroed)."""
+    """P: coarse vector -> fine vector, rows/columns of constrained DoFs removed (zeroed).
+    P depends only on the grids, so it is built once per grid pair and reused."""
+    key = (fine.n, coarse.n, fine.w_essential, coarse.w_essential)
+    if key not in _CACHE:
+        _CACHE[key] = _prolongation(fine, coarse)
+    return _CACHE[key].copy()
+
+
+def _prolongation(fine: Mesh, coarse: Mesh) -> sp.csr_matrix:
     assert fine.n == 2 * coarse.n
     h = fine.h
     H = coarse.h
