@@ -1,0 +1,208 @@
+/*
+ * biotmg.h -- C ABI of the GB300 (sm_103a) monolithic-multigrid solver for the
+ * reduced-quadrature three-field Biot system of Adler, He, Hu, MacLachlan and Ohm,
+ * "Monolithic multigrid for a reduced-quadrature discretization of poroelasticity"
+ * (arXiv 2107.04060).
+ *
+ * Problem (Sec. 2.1 Eqs. discrete1-3, Sec. 2.3 Eq. block_form_rq): one backward-Euler step
+ * of Biot's model on the unit square, discretised with P1-plus-face-bubble displacement,
+ * lowest-order Raviart-Thomas Darcy velocity and P0 pressure on the uniform triangulation
+ * of App. A (n x n squares, each cut along the diagonal from top-left to bottom-right),
+ * with the reduced-quadrature grad-div term lambda (P_Q div u, P_Q div v):
+ *
+ *        | A_u^RQ      0          alpha B_u^T |
+ *    A = | 0           tau M_w    tau B_w^T   |    A_u^RQ = 2 mu A_eps + lambda B_u^T M_p^{-1} B_u
+ *        | alpha B_u   tau B_w    -(1/M) M_p  |
+ *
+ * Displacement is zero on the whole boundary; the pressure condition is natural (RT0
+ * boundary fluxes are unknowns).  The solver is right-preconditioned FGMRES (Sec. 5.1)
+ * with one monolithic V-cycle (Sec. 3, Eq. TG-Operator-Biot): additive Vanka on vertex
+ * patches (Sec. 3.2.1) or inexact Braess-Sarazin (Sec. 3.2.2, App. D), the block
+ * interpolation P = diag(P_u, P_w, P_p) with divergence-preserving P_u (Sec. 3.1), R = P^T,
+ * rediscretised coarse operators and a direct solve on the coarsest grid (Sec. 5.1).
+ *
+ * ---------------------------------------------------------------------------------------
+ * VECTOR LAYOUT (every vector argument).  A vector on an n-cell grid is 10 blocks, in the
+ * order  ux, uy, bh, bv, bd, wh, wv, wd, pL, pU :
+ *   ux, uy  P1 displacement at vertex (i, j)           0 <= i, j <= n
+ *   bh, wh  bubble / RT0 on the edge (i,j)-(i+1,j)      0 <= i < n, 0 <= j <= n
+ *   bv, wv  bubble / RT0 on the edge (i,j)-(i,j+1)      0 <= i <= n, 0 <= j < n
+ *   bd, wd  bubble / RT0 on the diagonal of cell (i,j)  0 <= i, j < n
+ *   pL, pU  P0 on the lower-left / upper-right triangle of cell (i, j)
+ * Each block is (n+1) rows (j) of bmg_pitch(n) elements (i); element (i, j) of block k sits
+ * at  k * bmg_block_len(n) + j * bmg_pitch(n) + i.  Slots outside the ranges above and the
+ * constrained displacement slots (ux, uy on boundary vertices; bh on j = 0, n; bv on
+ * i = 0, n) must hold 0 on input and are written as 0 on output.  Norms are Euclidean over
+ * the whole vector (hence over the free DoFs).  Bubble coefficients are the normal
+ * displacement at the edge midpoint (basis 4 l_a l_b n_e, n_h = (0,1), n_v = (1,0),
+ * n_d = (1,1)/sqrt 2); RT0 coefficients are the normal flux density along the same normals.
+ *
+ * CONVENTIONS.  All pointers to vector or field data are DEVICE pointers unless the name
+ * says _host.  Vectors are caller-owned; handles own every internal buffer.  `stream` is a
+ * cudaStream_t (NULL = legacy default stream); every call is stream-ordered.  Calls return
+ * BMG_OK (0) or a negative BMG_ERR_* code; bmg_status_string() describes a code.  A
+ * non-converged solve is not an error: it is reported in bmg_solve_info.status.  Handles
+ * are not thread-safe; distinct handles may be used concurrently on distinct streams.
+ * There is no CPU fallback: without a usable CUDA device every call fails with
+ * BMG_ERR_CUDA.
+ */
+#ifndef BIOTMG_H
+#define BIOTMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------------------ */
+#define BMG_OK 0
+#define BMG_ERR_ARG (-1)      /* invalid argument (size, pointer, option)              */
+#define BMG_ERR_CUDA (-2)     /* CUDA runtime error (see bmg_last_error)               */
+#define BMG_ERR_ALLOC (-3)    /* device or host allocation failed                      */
+#define BMG_ERR_SINGULAR (-4) /* a patch or coarse-grid factorisation met a zero pivot */
+#define BMG_ERR_NONFINITE (-5)/* non-finite input (right-hand side or coefficients)    */
+
+/* ---- solve status (bmg_solve_info.status) ------------------------------------------ */
+#define BMG_CONVERGED 0
+#define BMG_MAXIT 1           /* iteration limit reached before the tolerance          */
+#define BMG_BREAKDOWN 2       /* Arnoldi breakdown (h_{j+1,j} = 0) without convergence */
+#define BMG_DIVERGED 3        /* non-finite residual                                   */
+
+/* ---- options ----------------------------------------------------------------------- */
+#define BMG_VANKA 0           /* additive Vanka, 20-DoF vertex patches (Sec. 3.2.1)     */
+#define BMG_BSR 1             /* inexact Braess-Sarazin (Sec. 3.2.2, App. D)            */
+#define BMG_FP64 0
+#define BMG_FP32 1
+
+typedef struct bmg_system bmg_system;       /* one assembled operator (FP64)           */
+typedef struct bmg_hierarchy bmg_hierarchy; /* multigrid preconditioner for a system   */
+
+/* Layout helpers: row pitch (elements), block length, vector length, for n cells/side. */
+int bmg_pitch(int n);
+size_t bmg_block_len(int n);
+size_t bmg_vector_len(int n);
+
+/* Number of free (unconstrained) DoFs of an n-cell grid: 2(n-1)^2 displacement P1 values,
+ * the bubbles on the 3n^2 - 2n interior edges, RT0 on all 3n^2 + 2n edges, 2n^2 pressures. */
+size_t bmg_free_dofs(int n);
+
+/*
+ * bmg_assemble -- operator coefficients (Sec. 2.1 Eq. block_form; Sec. 2.3 a^RQ; App. A).
+ *   n        cells per side, 1 <= n <= 16384 (multigrid needs n = n_coarse * 2^k).
+ *   lambda, mu  Lame coefficients (> 0 and >= 0 respectively, finite).
+ *   K        device pointer to per-triangle permeability, FP64, two blocks (L then U) of
+ *            (n+1) x bmg_pitch(n) laid out like a vector block ([j][i], i, j < n used);
+ *            may be NULL, then the permeability is K_const everywhere.  mu_f = 1.
+ *   K_const  uniform permeability (> 0) used when K is NULL.
+ *   tau      time step (> 0);  alpha  Biot-Willis constant;  inv_M  1/M (>= 0).
+ * The permeability is read once (converted to K^{-1}); the caller keeps ownership.
+ * On success *out receives a new system (free with bmg_destroy_system).
+ * Errors: BMG_ERR_ARG (bad sizes/parameters), BMG_ERR_NONFINITE (K <= 0 or non-finite),
+ * BMG_ERR_ALLOC, BMG_ERR_CUDA.
+ */
+int bmg_assemble(int n, double lambda, double mu, const double *K, double K_const,
+                 double tau, double alpha, double inv_M, void *stream, bmg_system **out);
+
+/*
+ * bmg_apply -- y = A x (FP64, matrix-free).  bmg_residual -- r = b - A x.
+ * x, y, b, r: device vectors of bmg_vector_len(n) doubles; y/r may not alias x.
+ */
+int bmg_apply(const bmg_system *s, const double *x, double *y, void *stream);
+int bmg_residual(const bmg_system *s, const double *b, const double *x, double *r,
+                 void *stream);
+
+typedef struct {
+  int smoother;     /* BMG_VANKA or BMG_BSR                                           */
+  int nu1, nu2;     /* pre-/post-relaxation sweeps (>= 0)                             */
+  double omega;     /* outer relaxation weight (Sec. 3.2: E_s = I - omega M^{-1} A)    */
+  double omega_J;   /* Jacobi weight on the Schur complement (BSR only, App. D)        */
+  int n_coarse;     /* coarsest grid (cells per side) for the direct solve, e.g. 8     */
+  int precision;    /* BMG_FP64 or BMG_FP32 arithmetic inside the V-cycle             */
+  double p_shift;   /* >= 0: -p_shift * |T| is added to every P0 diagonal entry of the
+                       Vanka patch matrices (the regularisation of Sec. 5.3 for 1/M = 0;
+                       0 = exact patch solves)                                          */
+} bmg_mg_opts;
+
+/*
+ * bmg_setup_hierarchy -- multigrid hierarchy for system s (Sec. 3): levels n, n/2, ...,
+ * n_coarse with rediscretised operators (the coarse RT0 mass is P_w^T M_w P_w, which is
+ * the rediscretisation with the fine-scale K^{-1}); FP64 factorisation of every distinct
+ * Vanka patch matrix (Gauss-Jordan with partial pivoting); FP64 inverse of the coarsest
+ * operator.  The hierarchy keeps a pointer to s: s must outlive it.
+ * Errors: BMG_ERR_ARG (n not n_coarse * 2^k, bad options), BMG_ERR_SINGULAR, BMG_ERR_ALLOC,
+ * BMG_ERR_CUDA.
+ */
+int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, void *stream,
+                        bmg_hierarchy **out);
+
+/*
+ * bmg_vcycle -- z = M^{-1} r: one V(nu1, nu2) cycle from a zero initial guess (Sec. 3).
+ * r, z: device vectors (bmg_vector_len(n) doubles, FP64 whatever the V-cycle precision;
+ * an FP32 hierarchy converts on entry and exit).  z may not alias r.
+ */
+int bmg_vcycle(bmg_hierarchy *h, const double *r, double *z, void *stream);
+
+typedef struct {
+  double rtol;      /* stop when ||b - A x|| <= rtol ||b|| (true residual), e.g. 1e-8  */
+  int restart;      /* FGMRES restart length m (1..200)                                */
+  int maxit;        /* total iteration limit                                           */
+  int x0_is_zero;   /* 1: ignore the contents of x on entry; 0: use x as initial guess */
+} bmg_krylov_opts;
+
+typedef struct {
+  int iters;        /* FGMRES iterations (preconditioner applications)                 */
+  int restarts;     /* restart cycles started                                          */
+  int status;       /* BMG_CONVERGED, BMG_MAXIT, BMG_BREAKDOWN or BMG_DIVERGED         */
+  double relres;    /* final true relative residual ||b - A x|| / ||b||                */
+  double relres_est;/* final Arnoldi estimate |g_{j+1}| / ||b||                        */
+  double solve_ms;  /* wall time of the call (host clock, includes the final sync)     */
+} bmg_solve_info;
+
+/*
+ * bmg_fgmres_solve -- x ~= A^{-1} b by right-preconditioned flexible GMRES(m) with one
+ * V-cycle of h as the preconditioner (Sec. 5.1).  Arnoldi by classical Gram-Schmidt with
+ * one re-orthogonalisation pass, all in FP64.  b, x: device vectors.  The call returns
+ * after the solve has finished (it synchronises `stream` once per iteration to read the
+ * Hessenberg column).  info may be NULL.
+ */
+int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
+                     const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
+
+/* Same with HOST vectors: copies b in, solves, copies x out (all on `stream`). */
+int bmg_fgmres_solve_host(bmg_hierarchy *h, const double *b_host, double *x_host,
+                          const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
+
+/*
+ * Kernel timing (tracing).  bmg_profile_start(kernel, n) makes every later launch of the
+ * named kernel family on an n-cell grid (n = 0: any grid) bracket itself with a pair of CUDA
+ * events on its own stream; bmg_profile_stop() synchronises those events and returns the
+ * summed device time (ms), the number of launches and the number of grid cells the launches
+ * processed (n*n per launch, times the batch).  Only one kernel family is timed at a time.
+ * Timing adds two event records per timed launch and nothing else.
+ */
+#define BMG_PROF_APPLY 1      /* matrix-free operator application / residual           */
+#define BMG_PROF_VANKA 2      /* additive Vanka sweep (20-DoF patches)                  */
+#define BMG_PROF_VANKA_U 3    /* displacement Vanka + Jacobi step inside BSR            */
+#define BMG_PROF_RESTRICT 4
+#define BMG_PROF_PROLONG 5
+#define BMG_PROF_COARSE 6     /* coarsest-grid solve                                   */
+#define BMG_PROF_KRYLOV 7     /* FGMRES vector kernels (dots, updates, scaling)         */
+int bmg_profile_start(int kernel, int n);
+int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
+
+/* Grid size of a system / hierarchy (cells per side). */
+int bmg_system_n(const bmg_system *s);
+int bmg_hierarchy_levels(const bmg_hierarchy *h);
+
+void bmg_destroy_system(bmg_system *s);
+void bmg_destroy_hierarchy(bmg_hierarchy *h);
+
+/* Text for a return code; bmg_last_error: detail of the last failure on this thread. */
+const char *bmg_status_string(int code);
+const char *bmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIOTMG_H */

@@ -1,0 +1,615 @@
+// C ABI of the library (include/biotmg.h): systems, hierarchies, the V-cycle and FGMRES.
+// Host code only orchestrates: every arithmetic step of assembly, relaxation, transfer,
+// coarse solve and Krylov iteration runs in this library's kernels.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bmg_internal.h"
+
+namespace bmg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return BMG_ERR_CUDA;
+}
+
+static int arg_error(const std::string &msg) {
+  g_last_error = msg;
+  return BMG_ERR_ARG;
+}
+
+// ---- coefficient kernels ---------------------------------------------------------------
+__global__ void kinv_from_k_kernel(Grid g, const double *K, double *kinv64, float *kinv32,
+                                   int *flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.pitch || j > g.n) return;
+  for (int o = 0; o < 2; ++o) {
+    const size_t idx = (size_t)o * g.blk + (size_t)j * g.pitch + i;
+    double v = 0.0;
+    if (i < g.n && j < g.n) {
+      const double k = K[idx];
+      if (!(k > 0.0) || !isfinite(k)) atomicOr(flag, 4);
+      else v = 1.0 / k;
+    }
+    kinv64[idx] = v;
+    kinv32[idx] = (float)v;
+  }
+}
+
+static int alloc_coefs(Level &L, bool full) {
+  const size_t blk = L.g.blk;
+  if (!full) {
+    BMG_CUDA(cudaMalloc(&L.kinv64, sizeof(double) * 2 * blk));
+    BMG_CUDA(cudaMalloc(&L.kinv32, sizeof(float) * 2 * blk));
+  } else {
+    BMG_CUDA(cudaMalloc(&L.wm64, sizeof(double) * 12 * blk));
+    BMG_CUDA(cudaMalloc(&L.wm32, sizeof(float) * 12 * blk));
+    BMG_CUDA(cudaMemset(L.wm64, 0, sizeof(double) * 12 * blk));
+    BMG_CUDA(cudaMemset(L.wm32, 0, sizeof(float) * 12 * blk));
+  }
+  return BMG_OK;
+}
+
+static void free_level(Level &L) {
+  if (L.owns_coefs) {
+    cudaFree(L.kinv64); cudaFree(L.kinv32); cudaFree(L.wm64); cudaFree(L.wm32);
+  }
+  cudaFree(L.slot); cudaFree(L.pinv64); cudaFree(L.pinv32);
+  cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
+  cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
+  cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2);
+  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.bry);
+  L = Level();
+}
+
+// ---- kernel timing ---------------------------------------------------------------------
+struct ProfState {
+  int kernel = 0, n = 0;
+  std::vector<cudaEvent_t> ev;     // pairs (begin, end)
+  double cells = 0.0;
+};
+static ProfState g_prof;
+
+bool prof_on(int kernel, int n) {
+  return g_prof.kernel != 0 && g_prof.kernel == kernel && (g_prof.n == 0 || g_prof.n == n);
+}
+void prof_begin(cudaStream_t st) {
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  g_prof.ev.push_back(e);
+}
+void prof_end(cudaStream_t st, double cells) {
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, st);
+  g_prof.ev.push_back(e);
+  g_prof.cells += cells;
+}
+
+}  // namespace bmg
+
+using namespace bmg;
+
+extern "C" int bmg_profile_start(int kernel, int n) {
+  if (kernel < 1 || kernel > 7 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");
+  for (auto e : g_prof.ev) cudaEventDestroy(e);
+  g_prof = ProfState();
+  g_prof.kernel = kernel;
+  g_prof.n = n;
+  return BMG_OK;
+}
+
+extern "C" int bmg_profile_stop(double *total_ms, long long *launches, double *cells) {
+  double tot = 0.0;
+  long long cnt = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t k = 0; k + 1 < g_prof.ev.size(); k += 2) {
+    cudaError_t e = cudaEventSynchronize(g_prof.ev[k + 1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, g_prof.ev[k], g_prof.ev[k + 1]);
+    if (e != cudaSuccess) err = e;
+    tot += ms;
+    ++cnt;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = cnt;
+  if (cells) *cells = g_prof.cells;
+  for (auto e : g_prof.ev) cudaEventDestroy(e);
+  g_prof = ProfState();
+  if (err != cudaSuccess) return cuda_fail(err, "bmg_profile_stop");
+  return BMG_OK;
+}
+
+// ---- layout ----------------------------------------------------------------------------
+extern "C" int bmg_pitch(int n) { return n >= 1 ? pitch_of(n) : 0; }
+extern "C" size_t bmg_block_len(int n) { return n >= 1 ? block_len_of(n) : 0; }
+extern "C" size_t bmg_vector_len(int n) { return n >= 1 ? vec_len_of(n) : 0; }
+extern "C" size_t bmg_free_dofs(int n) {
+  if (n < 1) return 0;
+  const size_t N = (size_t)n;
+  return 2 * (N - 1) * (N - 1) + (3 * N * N - 2 * N) + (3 * N * N + 2 * N) + 2 * N * N;
+}
+
+extern "C" const char *bmg_status_string(int code) {
+  switch (code) {
+    case BMG_OK: return "ok";
+    case BMG_ERR_ARG: return "invalid argument";
+    case BMG_ERR_CUDA: return "CUDA error";
+    case BMG_ERR_ALLOC: return "allocation failed";
+    case BMG_ERR_SINGULAR: return "singular factorisation";
+    case BMG_ERR_NONFINITE: return "non-finite or non-positive input";
+    default: return "unknown status";
+  }
+}
+extern "C" const char *bmg_last_error(void) { return g_last_error.c_str(); }
+
+// ---- system ----------------------------------------------------------------------------
+extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, double K_const,
+                            double tau, double alpha, double inv_M, void *stream,
+                            bmg_system **out) {
+  if (!out) return arg_error("bmg_assemble: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 16384) return arg_error("bmg_assemble: n out of range [1, 16384]");
+  if (!(std::isfinite(lambda) && lambda > 0.0) || !(std::isfinite(mu) && mu >= 0.0) ||
+      !(std::isfinite(tau) && tau > 0.0) || !std::isfinite(alpha) ||
+      !(std::isfinite(inv_M) && inv_M >= 0.0))
+    return arg_error("bmg_assemble: physical parameters must be finite with lambda > 0, "
+                     "mu >= 0, tau > 0, inv_M >= 0");
+  if (!K && !(std::isfinite(K_const) && K_const > 0.0))
+    return arg_error("bmg_assemble: K_const must be finite and > 0 when K is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = upload_transfer_tables();
+  if (rc) return rc;
+  bmg_system *s = new bmg_system();
+  s->n = n;
+  s->prm = PhysParams{lambda, mu, tau, alpha, inv_M};
+  s->uniform = (K == nullptr);
+  s->K_const = K_const;
+  Level &L = s->fine;
+  L.n = n;
+  L.g = grid_of(n);
+  L.uniform = s->uniform;
+  rc = alloc_coefs(L, false);
+  if (rc) { free_level(L); delete s; return rc; }
+  make_coefs(s->prm, n, &L.c64, &L.c32);
+  if (s->uniform) {
+    if ((rc = launch_fill<double>(L.kinv64, 1.0 / K_const, 2 * L.g.blk, st)) ||
+        (rc = launch_fill<float>(L.kinv32, (float)(1.0 / K_const), 2 * L.g.blk, st))) {
+      free_level(L); delete s; return rc;
+    }
+  } else {
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e != cudaSuccess) { free_level(L); delete s; return cuda_fail(e, "cudaMalloc(flag)"); }
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    dim3 b(32, 8), gr((L.g.pitch + 31) / 32, (n + 1 + 7) / 8);
+    kinv_from_k_kernel<<<gr, b, 0, st>>>(L.g, K, L.kinv64, L.kinv32, flag);
+    int hflag = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(flag);
+    if (e != cudaSuccess) { free_level(L); delete s; return cuda_fail(e, "kinv_from_k"); }
+    if (hflag) {
+      free_level(L); delete s;
+      set_error("bmg_assemble: permeability must be finite and > 0 on every triangle");
+      return BMG_ERR_NONFINITE;
+    }
+  }
+  *out = s;
+  return BMG_OK;
+}
+
+extern "C" int bmg_system_n(const bmg_system *s) { return s ? s->n : 0; }
+
+extern "C" void bmg_destroy_system(bmg_system *s) {
+  if (!s) return;
+  free_level(s->fine);
+  delete s;
+}
+
+extern "C" int bmg_apply(const bmg_system *s, const double *x, double *y, void *stream) {
+  if (!s || !x || !y) return arg_error("bmg_apply: NULL argument");
+  if (x == y) return arg_error("bmg_apply: y may not alias x");
+  return launch_apply<double>(s->fine, x, nullptr, y, false, 1, 0, (cudaStream_t)stream);
+}
+
+extern "C" int bmg_residual(const bmg_system *s, const double *b, const double *x, double *r,
+                            void *stream) {
+  if (!s || !b || !x || !r) return arg_error("bmg_residual: NULL argument");
+  if (x == r) return arg_error("bmg_residual: r may not alias x");
+  return launch_apply<double>(s->fine, x, b, r, true, 1, 0, (cudaStream_t)stream);
+}
+
+// ---- hierarchy -------------------------------------------------------------------------
+static int setup_patches(bmg_hierarchy *h, Level &L, int psize, double p_shift,
+                         cudaStream_t st) {
+  const int n = L.n;
+  std::vector<int> slot((size_t)(n + 1) * (n + 1));
+  std::vector<int> ri, rj;
+  if (L.uniform && n >= 2) {
+    ri.push_back(1);
+    rj.push_back(1);
+    for (int j = 0; j <= n; ++j)
+      for (int i = 0; i <= n; ++i) {
+        const bool interior = i > 0 && i < n && j > 0 && j < n;
+        if (interior) {
+          slot[(size_t)j * (n + 1) + i] = 0;
+        } else {
+          slot[(size_t)j * (n + 1) + i] = (int)ri.size();
+          ri.push_back(i);
+          rj.push_back(j);
+        }
+      }
+  } else {
+    for (int j = 0; j <= n; ++j)
+      for (int i = 0; i <= n; ++i) {
+        slot[(size_t)j * (n + 1) + i] = (int)ri.size();
+        ri.push_back(i);
+        rj.push_back(j);
+      }
+  }
+  const int nrep = (int)ri.size();
+  L.nslots = nrep;
+  L.psize = psize;
+  int *d_ri = nullptr, *d_rj = nullptr;
+  BMG_CUDA(cudaMalloc(&L.slot, sizeof(int) * slot.size()));
+  BMG_CUDA(cudaMalloc(&d_ri, sizeof(int) * nrep));
+  BMG_CUDA(cudaMalloc(&d_rj, sizeof(int) * nrep));
+  BMG_CUDA(cudaMalloc(&L.pinv64, sizeof(double) * (size_t)psize * psize * nrep));
+  BMG_CUDA(cudaMalloc(&L.pinv32, sizeof(float) * (size_t)psize * psize * nrep));
+  BMG_CUDA(cudaMemcpyAsync(L.slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice, st));
+  BMG_CUDA(cudaMemcpyAsync(d_ri, ri.data(), sizeof(int) * nrep, cudaMemcpyHostToDevice, st));
+  BMG_CUDA(cudaMemcpyAsync(d_rj, rj.data(), sizeof(int) * nrep, cudaMemcpyHostToDevice, st));
+  int rc = launch_vanka_setup(L, d_ri, d_rj, nrep, p_shift * 0.5 / ((double)n * n), psize,
+                              h->d_flag, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(d_ri);
+  cudaFree(d_rj);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "vanka setup");
+  return BMG_OK;
+}
+
+extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, void *stream,
+                                   bmg_hierarchy **out) {
+  if (!out) return arg_error("bmg_setup_hierarchy: out is NULL");
+  *out = nullptr;
+  if (!s || !o) return arg_error("bmg_setup_hierarchy: NULL argument");
+  if (o->smoother != BMG_VANKA && o->smoother != BMG_BSR)
+    return arg_error("bmg_setup_hierarchy: unknown smoother");
+  if (o->precision != BMG_FP64 && o->precision != BMG_FP32)
+    return arg_error("bmg_setup_hierarchy: unknown precision");
+  if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16)
+    return arg_error("bmg_setup_hierarchy: need 0 <= nu1, nu2 <= 16 and nu1 + nu2 >= 1");
+  if (!(std::isfinite(o->omega) && o->omega > 0.0) || !std::isfinite(o->omega_J) ||
+      !(std::isfinite(o->p_shift) && o->p_shift >= 0.0))
+    return arg_error("bmg_setup_hierarchy: omega > 0, finite omega_J, p_shift >= 0 required");
+  const int n = s->n;
+  if (o->n_coarse < 2 || o->n_coarse > 64 || n < o->n_coarse || n % o->n_coarse)
+    return arg_error("bmg_setup_hierarchy: need 2 <= n_coarse <= 64 dividing n");
+  int ratio = n / o->n_coarse;
+  if (ratio & (ratio - 1)) return arg_error("bmg_setup_hierarchy: n / n_coarse must be a power of 2");
+  cudaStream_t st = (cudaStream_t)stream;
+  bmg_hierarchy *h = new bmg_hierarchy();
+  h->sys = s;
+  h->opts = *o;
+  auto fail = [&](int rc) {
+    bmg_destroy_hierarchy(h);
+    return rc;
+  };
+  if (cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation, "flag"));
+  cudaMemsetAsync(h->d_flag, 0, sizeof(int), st);
+  const bool fp32 = o->precision == BMG_FP32;
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  for (int m = n;; m /= 2) {
+    h->levels.emplace_back();
+    Level &L = h->levels.back();
+    L.n = m;
+    L.g = grid_of(m);
+    if (m == n) {
+      L.owns_coefs = false;
+      L.kinv64 = s->fine.kinv64;
+      L.kinv32 = s->fine.kinv32;
+      L.c64 = s->fine.c64;
+      L.c32 = s->fine.c32;
+      L.uniform = s->uniform;
+      L.wm_full = false;
+    } else {
+      L.uniform = s->uniform;
+      L.wm_full = !s->uniform;
+      int rc = alloc_coefs(L, L.wm_full);
+      if (rc) return fail(rc);
+      make_coefs(s->prm, m, &L.c64, &L.c32);
+      if (s->uniform) {
+        if ((rc = launch_fill<double>(L.kinv64, 1.0 / s->K_const, 2 * L.g.blk, st)) ||
+            (rc = launch_fill<float>(L.kinv32, (float)(1.0 / s->K_const), 2 * L.g.blk, st)))
+          return fail(rc);
+      } else {
+        rc = launch_coarsen_wmass(h->levels[h->levels.size() - 2], L, st);
+        if (rc) return fail(rc);
+      }
+    }
+    const size_t vl = vec_len_of(m);
+    if (cudaMalloc(&L.rhs, es * vl) != cudaSuccess || cudaMalloc(&L.z, es * vl) != cudaSuccess ||
+        cudaMalloc(&L.t, es * vl) != cudaSuccess || cudaMalloc(&L.t2, es * vl) != cudaSuccess)
+      return fail(cuda_fail(cudaErrorMemoryAllocation, "level work vectors"));
+    cudaMemsetAsync(L.rhs, 0, es * vl, st);
+    cudaMemsetAsync(L.z, 0, es * vl, st);
+    cudaMemsetAsync(L.t, 0, es * vl, st);
+    cudaMemsetAsync(L.t2, 0, es * vl, st);
+    if (m == o->n_coarse) break;
+  }
+  for (size_t l = 0; l + 1 < h->levels.size(); ++l) {
+    Level &L = h->levels[l];
+    int rc;
+    if (o->smoother == BMG_VANKA) {
+      rc = setup_patches(h, L, 20, o->p_shift, st);
+    } else {
+      rc = setup_patches(h, L, 8, 0.0, st);
+      const PhysParams &p = s->prm;
+      const double area = 0.5 / ((double)L.n * L.n);
+      const double c_fs = p.inv_M + p.alpha * p.alpha / (p.lambda + p.mu);   // 2 mu / d, d = 2
+      if (!rc) rc = launch_bsr_setup(L, o->omega_J, c_fs * area, st);
+      const size_t vl = vec_len_of(L.n);
+      if (!rc && (cudaMalloc(&L.bz, es * vl) != cudaSuccess || cudaMalloc(&L.bd, es * vl) != cudaSuccess ||
+                  cudaMalloc(&L.bry, es * vl) != cudaSuccess))
+        rc = cuda_fail(cudaErrorMemoryAllocation, "BSR work vectors");
+      if (!rc) {
+        cudaMemsetAsync(L.bz, 0, es * vl, st);
+        cudaMemsetAsync(L.bd, 0, es * vl, st);
+        cudaMemsetAsync(L.bry, 0, es * vl, st);
+      }
+    }
+    if (rc) return fail(rc);
+  }
+  int rc = coarse_setup(h->levels.back(), h->d_flag, st);
+  if (rc) return fail(rc);
+  int hflag = 0;
+  cudaError_t e = cudaMemcpyAsync(&hflag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "bmg_setup_hierarchy"));
+  if (hflag) {
+    set_error(hflag & 1 ? "a Vanka patch matrix is singular" : "the coarsest operator is singular");
+    return fail(BMG_ERR_SINGULAR);
+  }
+  *out = h;
+  return BMG_OK;
+}
+
+extern "C" int bmg_hierarchy_levels(const bmg_hierarchy *h) { return h ? (int)h->levels.size() : 0; }
+
+extern "C" void bmg_destroy_hierarchy(bmg_hierarchy *h) {
+  if (!h) return;
+  for (auto &L : h->levels) free_level(L);
+  cudaFree(h->d_flag);
+  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r); cudaFree(h->xb);
+  cudaFree(h->partial); cudaFree(h->dres);
+  cudaFreeHost(h->hres);
+  cudaFree(h->hostbuf_b); cudaFree(h->hostbuf_x);
+  delete h;
+}
+
+// ---- V-cycle ---------------------------------------------------------------------------
+template <typename T>
+static int smooth(bmg_hierarchy *h, const Level &L, const T *r, T *x, cudaStream_t st) {
+  if (h->opts.smoother == BMG_VANKA) return launch_vanka_sweep<T>(L, r, x, (T)h->opts.omega, st);
+  return launch_bsr_sweep<T>(L, r, x, (T)h->opts.omega, st);
+}
+
+template <typename T>
+static int vcycle_level(bmg_hierarchy *h, size_t l, const T *rhs, T *z, cudaStream_t st) {
+  const Level &L = h->levels[l];
+  if (l + 1 == h->levels.size()) return launch_coarse_solve<T>(L, rhs, z, st);
+  int rc;
+  const size_t vl = vec_len_of(L.n);
+  T *t = (T *)L.t;
+  if ((rc = launch_fill<T>(z, T(0), vl, st))) return rc;
+  for (int s = 0; s < h->opts.nu1; ++s) {
+    if (s == 0) {
+      rc = smooth<T>(h, L, rhs, z, st);          // zero initial guess: residual = rhs
+    } else {
+      if ((rc = launch_apply<T>(L, z, rhs, t, true, 1, 0, st))) return rc;
+      rc = smooth<T>(h, L, t, z, st);
+    }
+    if (rc) return rc;
+  }
+  const T *res = rhs;
+  if (h->opts.nu1 > 0) {
+    if ((rc = launch_apply<T>(L, z, rhs, t, true, 1, 0, st))) return rc;
+    res = t;
+  }
+  const Level &C = h->levels[l + 1];
+  if ((rc = launch_restrict<T>(L, C, res, (T *)C.rhs, st))) return rc;
+  if ((rc = vcycle_level<T>(h, l + 1, (const T *)C.rhs, (T *)C.z, st))) return rc;
+  if ((rc = launch_prolong_add<T>(L, C, (const T *)C.z, z, st))) return rc;
+  for (int s = 0; s < h->opts.nu2; ++s) {
+    if ((rc = launch_apply<T>(L, z, rhs, t, true, 1, 0, st))) return rc;
+    if ((rc = smooth<T>(h, L, t, z, st))) return rc;
+  }
+  return BMG_OK;
+}
+
+static int vcycle_any(bmg_hierarchy *h, const double *r, double *z, cudaStream_t st) {
+  if (h->opts.precision == BMG_FP64) return vcycle_level<double>(h, 0, r, z, st);
+  Level &L = h->levels[0];
+  const size_t vl = vec_len_of(L.n);
+  int rc = launch_convert_d2f(r, (float *)L.rhs, vl, st);
+  if (rc) return rc;
+  if ((rc = vcycle_level<float>(h, 0, (const float *)L.rhs, (float *)L.t2, st))) return rc;
+  return launch_convert_f2d((const float *)L.t2, z, vl, st);
+}
+
+extern "C" int bmg_vcycle(bmg_hierarchy *h, const double *r, double *z, void *stream) {
+  if (!h || !r || !z) return arg_error("bmg_vcycle: NULL argument");
+  if (r == z) return arg_error("bmg_vcycle: z may not alias r");
+  return vcycle_any(h, r, z, (cudaStream_t)stream);
+}
+
+// ---- FGMRES ----------------------------------------------------------------------------
+static const int kDotBlocks = 152 * 4;
+
+static int ensure_krylov(bmg_hierarchy *h, int m) {
+  if (h->m_alloc >= m) return BMG_OK;
+  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r);
+  cudaFree(h->partial); cudaFree(h->dres); cudaFreeHost(h->hres);
+  h->V = h->Z = h->w = h->r = h->partial = h->dres = h->hres = nullptr;
+  h->m_alloc = 0;
+  const size_t vl = vec_len_of(h->sys->n);
+  BMG_CUDA(cudaMalloc(&h->V, sizeof(double) * vl * (m + 1)));
+  BMG_CUDA(cudaMalloc(&h->Z, sizeof(double) * vl * m));
+  BMG_CUDA(cudaMalloc(&h->w, sizeof(double) * vl));
+  BMG_CUDA(cudaMalloc(&h->r, sizeof(double) * vl));
+  BMG_CUDA(cudaMalloc(&h->partial, sizeof(double) * kDotBlocks * (m + 2)));
+  BMG_CUDA(cudaMalloc(&h->dres, sizeof(double) * 4 * (m + 2)));
+  BMG_CUDA(cudaMallocHost(&h->hres, sizeof(double) * 4 * (m + 2)));
+  h->m_alloc = m;
+  return BMG_OK;
+}
+
+extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
+                                const bmg_krylov_opts *o, bmg_solve_info *info, void *stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!h || !b || !x || !o) return arg_error("bmg_fgmres_solve: NULL argument");
+  if (b == x) return arg_error("bmg_fgmres_solve: x may not alias b");
+  if (!(o->rtol > 0.0 && o->rtol < 1.0) || o->restart < 1 || o->restart > 200 || o->maxit < 0)
+    return arg_error("bmg_fgmres_solve: need 0 < rtol < 1, 1 <= restart <= 200, maxit >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int m = o->restart;
+  int rc = ensure_krylov(h, m);
+  if (rc) return rc;
+  const bmg_system *s = h->sys;
+  const size_t vl = vec_len_of(s->n);
+  double *hr = h->hres;
+  if (o->x0_is_zero && (rc = launch_fill<double>(x, 0.0, vl, st))) return rc;
+  // ||b||
+  if ((rc = launch_dots(nullptr, vl, 0, b, vl, h->partial, kDotBlocks, h->dres, st))) return rc;
+  BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BMG_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(hr[0]);
+  bmg_solve_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  inf.status = BMG_MAXIT;
+  if (!std::isfinite(bnorm)) {
+    set_error("bmg_fgmres_solve: right-hand side is not finite");
+    return BMG_ERR_NONFINITE;
+  }
+  if (bnorm == 0.0) {
+    if ((rc = launch_fill<double>(x, 0.0, vl, st))) return rc;
+    BMG_CUDA(cudaStreamSynchronize(st));
+    inf.status = BMG_CONVERGED;
+    if (info) *info = inf;
+    return BMG_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double & { return H[(size_t)i * m + j]; };
+  const size_t ldv = vl;
+  double est = 1.0;
+  for (;;) {
+    // true residual
+    if ((rc = launch_apply<double>(s->fine, x, b, h->r, true, 1, 0, st))) return rc;
+    if ((rc = launch_dots(nullptr, vl, 0, h->r, vl, h->partial, kDotBlocks, h->dres, st))) return rc;
+    BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BMG_CUDA(cudaStreamSynchronize(st));
+    const double beta = std::sqrt(hr[0]);
+    inf.relres = beta / bnorm;
+    if (!std::isfinite(beta)) { inf.status = BMG_DIVERGED; break; }
+    if (beta <= o->rtol * bnorm) { inf.status = BMG_CONVERGED; break; }
+    if (inf.iters >= o->maxit) { inf.status = BMG_MAXIT; break; }
+    if (inf.status == BMG_BREAKDOWN) break;
+    inf.restarts++;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+    if ((rc = launch_scale(h->r, h->V, h->dres + 3 * (m + 2), vl, st))) return rc;
+    int k = 0;
+    bool stop = false;
+    for (int j = 0; j < m && !stop; ++j) {
+      double *vj = h->V + (size_t)j * ldv;
+      double *zj = h->Z + (size_t)j * ldv;
+      if ((rc = vcycle_any(h, vj, zj, st))) return rc;
+      if ((rc = launch_apply<double>(s->fine, zj, nullptr, h->w, false, 1, 0, st))) return rc;
+      double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
+      if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d1, st))) return rc;
+      if ((rc = launch_update(h->w, h->V, ldv, j + 1, d1, vl, st))) return rc;
+      if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d2, st))) return rc;
+      if ((rc = launch_update(h->w, h->V, ldv, j + 1, d2, vl, st))) return rc;
+      if ((rc = launch_dots(nullptr, vl, 0, h->w, vl, h->partial, kDotBlocks, d3, st))) return rc;
+      BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
+      BMG_CUDA(cudaStreamSynchronize(st));
+      const double hn = std::sqrt(hr[2 * (m + 2)]);
+      bool finite = std::isfinite(hn);
+      for (int i = 0; i <= j; ++i) {
+        Hij(i, j) = hr[i] + hr[(m + 2) + i];
+        finite = finite && std::isfinite(Hij(i, j));
+      }
+      Hij(j + 1, j) = hn;
+      inf.iters++;
+      if (!finite) { inf.status = BMG_DIVERGED; stop = true; k = j; break; }
+      if (hn > 0.0) {
+        BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &Hij(j + 1, j), sizeof(double), cudaMemcpyHostToDevice, st));
+        if ((rc = launch_scale(h->w, h->V + (size_t)(j + 1) * ldv, h->dres + 3 * (m + 2), vl, st))) return rc;
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = den > 0 ? Hij(j, j) / den : 1.0;
+      sn[j] = den > 0 ? Hij(j + 1, j) / den : 0.0;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      k = j + 1;
+      est = std::fabs(g[j + 1]) / bnorm;
+      if (std::fabs(g[j + 1]) <= o->rtol * bnorm) stop = true;
+      else if (hn == 0.0) { stop = true; inf.status = BMG_BREAKDOWN; }
+      if (inf.iters >= o->maxit) stop = true;
+    }
+    if (inf.status == BMG_DIVERGED) break;
+    // y = H^{-1} g, x += Z y
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int c = i + 1; c < k; ++c) acc -= Hij(i, c) * y[c];
+      y[i] = Hij(i, i) != 0.0 ? acc / Hij(i, i) : 0.0;
+    }
+    BMG_CUDA(cudaMemcpyAsync(h->dres, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+    if ((rc = launch_axpy_multi(x, h->Z, ldv, k, h->dres, vl, st))) return rc;
+  }
+  BMG_CUDA(cudaStreamSynchronize(st));
+  inf.relres_est = est;
+  inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return BMG_OK;
+}
+
+extern "C" int bmg_fgmres_solve_host(bmg_hierarchy *h, const double *b_host, double *x_host,
+                                     const bmg_krylov_opts *o, bmg_solve_info *info,
+                                     void *stream) {
+  if (!h || !b_host || !x_host || !o) return arg_error("bmg_fgmres_solve_host: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vl = vec_len_of(h->sys->n);
+  if (!h->hostbuf_b) BMG_CUDA(cudaMalloc(&h->hostbuf_b, sizeof(double) * vl));
+  if (!h->hostbuf_x) BMG_CUDA(cudaMalloc(&h->hostbuf_x, sizeof(double) * vl));
+  BMG_CUDA(cudaMemcpyAsync(h->hostbuf_b, b_host, sizeof(double) * vl, cudaMemcpyHostToDevice, st));
+  if (!o->x0_is_zero)
+    BMG_CUDA(cudaMemcpyAsync(h->hostbuf_x, x_host, sizeof(double) * vl, cudaMemcpyHostToDevice, st));
+  int rc = bmg_fgmres_solve(h, h->hostbuf_b, h->hostbuf_x, o, info, stream);
+  if (rc) return rc;
+  BMG_CUDA(cudaMemcpyAsync(x_host, h->hostbuf_x, sizeof(double) * vl, cudaMemcpyDeviceToHost, st));
+  BMG_CUDA(cudaStreamSynchronize(st));
+  return BMG_OK;
+}

@@ -1,0 +1,214 @@
+// Internal declarations of the biotmg library (not part of the C ABI).
+//
+// Structured-grid layout: every DoF type of an n-cell grid lives in an (n+1) x pitch block
+// indexed [j][i]; see include/biotmg.h for the block order and the valid ranges.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/biotmg.h"
+
+namespace bmg {
+
+// DoF block order inside a vector.
+enum Block { UX = 0, UY, BH, BV, BD, WH, WV, WD, PL, PU, NBLK };
+
+inline int pitch_of(int n) { return ((n + 1) + 7) & ~7; }
+inline size_t block_len_of(int n) { return (size_t)(n + 1) * (size_t)pitch_of(n); }
+inline size_t vec_len_of(int n) { return (size_t)NBLK * block_len_of(n); }
+
+// Grid shape passed to every kernel.
+struct Grid {
+  int n;        // cells per side
+  int pitch;    // row pitch (elements)
+  size_t blk;   // elements per block
+};
+
+inline Grid grid_of(int n) { return Grid{n, pitch_of(n), block_len_of(n)}; }
+
+// --------------------------------------------------------------------------------------
+// Element integrals of one triangle shape (o = 0: lower-left L, o = 1: upper-right U),
+// local DoF order (ux v0..v2, uy v0..v2, bubble e0..e2 | RT0 e0..e2 | P0); local edge k is
+// opposite local vertex k.  L(i,j) = {(i,j), (i+1,j), (i,j+1)}, edges (d(i,j), v(i,j),
+// h(i,j)); U(i,j) = {(i+1,j+1), (i,j+1), (i+1,j)}, edges (d(i,j), v(i+1,j), h(i,j+1)).
+struct ElemIntegrals {
+  double Aeps[2][9][9];   // int eps(phi_a) : eps(phi_b)
+  double g[2][9];         // int div phi_a
+  double Mw[2][3][3];     // int psi_a . psi_b
+  double dw[2][3];        // int div psi_a
+  double area;            // |T| = h^2 / 2
+};
+void element_integrals(double h, ElemIntegrals *out);
+
+// Operator coefficients of one level in arithmetic type T (kernel parameter).
+//   y_u = A u + g s,  s = lam_area (g.u) - alpha p
+//   y_w = kinv_T (M1 w) - dw p        (or Wm_T w with a per-triangle 3x3 RT0 mass)
+//   y_p = -alpha (g.u) - dw.w - pp p
+template <typename T>
+struct OpCoefs {
+  T A[2][81];   // 2 mu Aeps
+  T g[2][9];
+  T M1[2][9];   // tau * Mw (unit permeability)
+  T dw[2][3];   // tau * dw
+  T lam_area;   // lambda / |T|
+  T alpha;
+  T pp;         // (1/M) |T|
+};
+
+struct PhysParams {
+  double lambda, mu, tau, alpha, inv_M;
+};
+
+void make_coefs(const PhysParams &p, int n, OpCoefs<double> *c64, OpCoefs<float> *c32);
+
+// --------------------------------------------------------------------------------------
+// Transfer stencil tables (pure geometry; identical on every level).
+//   prolongation: fine value (type t, parity class c = (i&1) + 2 (j&1)) at (i, j) =
+//       sum_k coef_k * coarse[ctype_k][(j>>1) + dJ_k][(i>>1) + dI_k]
+//   restriction:  coarse value (type t) at (I, J) = sum_k coef_k * fine[ftype_k][2J + dj_k][2I + di_k]
+struct StencilEntry {
+  int8_t type, di, dj, pad;
+  float pad2;
+  double coef;
+};
+constexpr int kMaxPro = 24;   // entries per (fine type, parity)
+constexpr int kMaxRes = 48;   // entries per coarse type
+struct TransferTables {
+  StencilEntry pro[NBLK][4][kMaxPro];
+  int npro[NBLK][4];
+  StencilEntry res[NBLK][kMaxRes];
+  int nres[NBLK];
+  // Galerkin coarsening of a per-triangle RT0 mass: coarse triangle (o) has children
+  // c = 0..3 of orientation child_o at fine cell (2I + cdi, 2J + cdj); Q maps the coarse
+  // triangle's 3 local RT0 DoFs to the child's 3 local RT0 DoFs.
+  int child_o[2][4], child_di[2][4], child_dj[2][4];
+  double Q[2][4][3][3];
+};
+void build_transfer_tables(TransferTables *t);
+
+// --------------------------------------------------------------------------------------
+struct Level {
+  int n = 0;
+  bool owns_coefs = true;      // false for a hierarchy's view of its system's fine level
+  Grid g{};
+  bool wm_full = false;        // per-triangle 3x3 RT0 mass (coarse levels, varying K)
+  bool uniform = false;        // every triangle has the same coefficients
+  double *kinv64 = nullptr;    // [2][blk] per-triangle K^{-1} (wm_full == false)
+  float *kinv32 = nullptr;
+  double *wm64 = nullptr;      // [2][6][blk] symmetric 3x3 RT0 mass incl. tau (wm_full)
+  float *wm32 = nullptr;
+  OpCoefs<double> c64{};
+  OpCoefs<float> c32{};
+  // additive Vanka (20-DoF patches) or the displacement Vanka inside BSR (8-DoF)
+  int nslots = 0;
+  int *slot = nullptr;         // [(n+1) * (n+1)] patch -> inverse slot
+  int psize = 0;               // 20 (Vanka) or 8 (BSR displacement patches)
+  double *pinv64 = nullptr;    // [psize*psize][nslots]
+  float *pinv32 = nullptr;
+  // BSR data
+  double *dinv64 = nullptr;    // [3][blk] 1 / (tau D_w) per edge family
+  float *dinv32 = nullptr;
+  double *sinv64 = nullptr;    // [2][blk] omega_J / diag(S) per triangle
+  float *sinv32 = nullptr;
+  void *bz = nullptr, *bd = nullptr, *bry = nullptr;   // BSR work vectors
+  // coarsest level: dense inverse on the free DoFs
+  int nfree = 0;
+  int *free_idx = nullptr;     // [nfree] vector positions of the free DoFs
+  double *cinv64 = nullptr;    // [nfree][nfree]
+  float *cinv32 = nullptr;
+  // work vectors in the V-cycle precision
+  void *rhs = nullptr, *z = nullptr, *t = nullptr, *t2 = nullptr;
+};
+
+}  // namespace bmg
+
+struct bmg_system {
+  int n;
+  bmg::PhysParams prm;
+  bool uniform;                // K given as a constant
+  double K_const;
+  bmg::Level fine;             // coefficients of the fine level (kinv64/kinv32, coefs)
+};
+
+struct bmg_hierarchy {
+  const bmg_system *sys;
+  bmg_mg_opts opts;
+  std::vector<bmg::Level> levels;
+  int *d_flag = nullptr;       // device error flag (singular pivots)
+  // FGMRES workspace (FP64)
+  int m_alloc = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *xb = nullptr;
+  double *partial = nullptr;   // [kMaxDot][nblocks]
+  double *dres = nullptr;      // device results of reductions
+  double *hres = nullptr;      // pinned host mirror
+  double *hostbuf_b = nullptr, *hostbuf_x = nullptr;   // device copies for the host API
+};
+
+// ---- error reporting ------------------------------------------------------------------
+namespace bmg {
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+}  // namespace bmg
+
+#define BMG_CUDA(call)                                               \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return bmg::cuda_fail(e_, #call);         \
+  } while (0)
+
+#define BMG_CHECK_LAUNCH(what)                                       \
+  do {                                                               \
+    cudaError_t e_ = cudaGetLastError();                             \
+    if (e_ != cudaSuccess) return bmg::cuda_fail(e_, what);          \
+  } while (0)
+
+// ---- kernel timing (bmg_profile_start / bmg_profile_stop) ------------------------------
+namespace bmg {
+bool prof_on(int kernel, int n);
+void prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st, double cells);
+}  // namespace bmg
+
+#define BMG_PROF_BEGIN(kid, n, st) const bool prof_ = bmg::prof_on(kid, n); if (prof_) bmg::prof_begin(st)
+#define BMG_PROF_END(st, cells) if (prof_) bmg::prof_end(st, cells)
+
+// ---- kernel launchers (implemented in the .cu files) -----------------------------------
+namespace bmg {
+template <typename T>
+int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, int batch,
+                 size_t bstride, cudaStream_t st);
+int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
+                       double p_shift_area, int psize, int *d_flag, cudaStream_t st);
+template <typename T>
+int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st);
+template <typename T>
+int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, cudaStream_t st);
+template <typename T>
+int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *xf,
+                       cudaStream_t st);
+int launch_coarsen_wmass(const Level &fine, Level &coarse, cudaStream_t st);
+int upload_transfer_tables();
+int coarse_setup(Level &L, int *d_flag, cudaStream_t st);
+template <typename T>
+int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st);
+int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st);
+template <typename T>
+int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st);
+// vector kernels
+template <typename T>
+int launch_fill(T *x, T v, size_t n, cudaStream_t st);
+int launch_convert_d2f(const double *x, float *y, size_t n, cudaStream_t st);
+int launch_convert_f2d(const float *x, double *y, size_t n, cudaStream_t st);
+int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n,
+                double *partial, int nblocks, double *out, cudaStream_t st);
+int launch_update(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                  cudaStream_t st);
+int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st);
+int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y,
+                      size_t n, cudaStream_t st);
+}  // namespace bmg

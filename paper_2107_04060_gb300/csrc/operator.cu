@@ -1,0 +1,287 @@
+// Matrix-free application of the reduced-quadrature Biot operator (Sec. 2.3,
+// Eq. block_form_rq) on the structured triangulation: y = A x or r = b - A x.
+//
+// Element-gather design: a CTA owns a 32 x 8 tile of output positions.  Phase 1 computes
+// the 13-entry local products of both triangles of every cell of the tile plus a one-cell
+// halo on the low side (the triangles that touch the tile's DoFs) into shared memory;
+// phase 2 gathers, for every DoF of the tile, the contributions of its triangles (6 for a
+// vertex, 2 for an edge, 1 for a triangle).  No atomics: the result is deterministic.
+// Constrained displacement slots are ignored on input and written as 0.
+#include "bmg_internal.h"
+#include "kernels_common.cuh"
+
+namespace bmg {
+
+template <typename T>
+struct ApplyArgs {
+  Grid g;
+  const T *x;
+  const T *b;        // residual mode only
+  T *y;
+  const T *kinv;     // [2][blk]          (WM == 0)
+  const T *wm;       // [2][6][blk]       (WM == 1)
+  size_t bstride;    // batch stride (elements) for batched application
+  int residual;
+  OpCoefs<T> c;
+};
+
+constexpr int kTX = 32, kTY = 8, kEX = kTX + 1, kEY = kTY + 1;
+
+// Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).
+template <typename T, int WM>
+__device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T u[9],
+                                            const T w[3], T p, T kinv, const T *wmT,
+                                            T *yl) {
+  T gu = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gu = fma(c.g[o][k], u[k], gu);
+  const T s = c.lam_area * gu - c.alpha * p;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    T acc = c.g[o][a] * s;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) acc = fma(c.A[o][a * 9 + b], u[b], acc);
+    yl[a] = acc;
+  }
+  T dww = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dww = fma(c.dw[o][k], w[k], dww);
+  if (WM == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T acc = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = fma(c.M1[o][a * 3 + b], w[b], acc);
+      yl[9 + a] = kinv * acc - c.dw[o][a] * p;
+    }
+  } else {
+    // symmetric 3x3: (00, 01, 02, 11, 12, 22)
+    yl[9] = wmT[0] * w[0] + wmT[1] * w[1] + wmT[2] * w[2] - c.dw[o][0] * p;
+    yl[10] = wmT[1] * w[0] + wmT[3] * w[1] + wmT[4] * w[2] - c.dw[o][1] * p;
+    yl[11] = wmT[2] * w[0] + wmT[4] * w[1] + wmT[5] * w[2] - c.dw[o][2] * p;
+  }
+  yl[12] = -c.alpha * gu - dww - c.pp * p;
+}
+
+template <typename T, int WM>
+__global__ void __launch_bounds__(kTX *kTY) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T(*sy)[26] = reinterpret_cast<T(*)[26]>(smem_raw);
+  const Grid g = a.g;
+  const int n = g.n, P = g.pitch;
+  const size_t blk = g.blk;
+  const size_t boff = (size_t)blockIdx.z * a.bstride;
+  const T *x = a.x + boff;
+  T *y = a.y + boff;
+  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
+  const int tid = threadIdx.y * kTX + threadIdx.x;
+
+  for (int e = tid; e < kEX * kEY; e += kTX * kTY) {
+    const int ci = i0 - 1 + e % kEX, cj = j0 - 1 + e / kEX;
+    T *yl = sy[e];
+    if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
+#pragma unroll
+      for (int k = 0; k < 26; ++k) yl[k] = 0;
+      continue;
+    }
+    const size_t c00 = (size_t)cj * P + ci;          // (ci, cj)
+    const size_t c10 = c00 + 1, c01 = c00 + P, c11 = c00 + P + 1;
+    const bool f00 = vfree(ci, cj, n), f10 = vfree(ci + 1, cj, n);
+    const bool f01 = vfree(ci, cj + 1, n), f11 = vfree(ci + 1, cj + 1, n);
+    const T ux00 = f00 ? x[UX * blk + c00] : T(0), uy00 = f00 ? x[UY * blk + c00] : T(0);
+    const T ux10 = f10 ? x[UX * blk + c10] : T(0), uy10 = f10 ? x[UY * blk + c10] : T(0);
+    const T ux01 = f01 ? x[UX * blk + c01] : T(0), uy01 = f01 ? x[UY * blk + c01] : T(0);
+    const T ux11 = f11 ? x[UX * blk + c11] : T(0), uy11 = f11 ? x[UY * blk + c11] : T(0);
+    const T bd = x[BD * blk + c00], wd = x[WD * blk + c00];
+    const T bhL = (cj > 0) ? x[BH * blk + c00] : T(0), whL = x[WH * blk + c00];
+    const T bvL = (ci > 0) ? x[BV * blk + c00] : T(0), wvL = x[WV * blk + c00];
+    const T bhU = (cj + 1 < n) ? x[BH * blk + c01] : T(0), whU = x[WH * blk + c01];
+    const T bvU = (ci + 1 < n) ? x[BV * blk + c10] : T(0), wvU = x[WV * blk + c10];
+    const T pL = x[PL * blk + c00], pU = x[PU * blk + c00];
+    T kL = 0, kU = 0;
+    T wmL[6], wmU[6];
+    if (WM == 0) {
+      kL = a.kinv[c00];
+      kU = a.kinv[blk + c00];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        wmL[k] = a.wm[(size_t)k * blk + c00];
+        wmU[k] = a.wm[(size_t)(6 + k) * blk + c00];
+      }
+    }
+    {  // L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj)
+      const T u[9] = {ux00, ux10, ux01, uy00, uy10, uy01, bd, bvL, bhL};
+      const T w[3] = {wd, wvL, whL};
+      tri_product<T, WM>(a.c, 0, u, w, pL, kL, wmL, yl);
+    }
+    {  // U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1)
+      const T u[9] = {ux11, ux01, ux10, uy11, uy01, uy10, bd, bvU, bhU};
+      const T w[3] = {wd, wvU, whU};
+      tri_product<T, WM>(a.c, 1, u, w, pU, kU, wmU, yl + 13);
+    }
+  }
+  __syncthreads();
+
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (j > n || i >= P) return;
+  const size_t o = (size_t)j * P + i;
+  if (i > n) {                                       // padding columns
+#pragma unroll
+    for (int k = 0; k < NBLK; ++k) y[k * blk + o] = 0;
+    return;
+  }
+  auto Y = [&](int ci, int cj, int k) -> T {
+    return sy[(cj - j0 + 1) * kEX + (ci - i0 + 1)][k];
+  };
+  T v[NBLK];
+  v[UX] = Y(i, j, 0) + Y(i - 1, j, 1) + Y(i, j - 1, 2) + Y(i - 1, j - 1, 13) +
+          Y(i, j - 1, 14) + Y(i - 1, j, 15);
+  v[UY] = Y(i, j, 3) + Y(i - 1, j, 4) + Y(i, j - 1, 5) + Y(i - 1, j - 1, 16) +
+          Y(i, j - 1, 17) + Y(i - 1, j, 18);
+  v[BH] = Y(i, j, 8) + Y(i, j - 1, 21);
+  v[BV] = Y(i, j, 7) + Y(i - 1, j, 20);
+  v[BD] = Y(i, j, 6) + Y(i, j, 19);
+  v[WH] = Y(i, j, 11) + Y(i, j - 1, 24);
+  v[WV] = Y(i, j, 10) + Y(i - 1, j, 23);
+  v[WD] = Y(i, j, 9) + Y(i, j, 22);
+  v[PL] = Y(i, j, 12);
+  v[PU] = Y(i, j, 25);
+  bool m[NBLK];
+  dof_masks(i, j, n, m);
+  const T *b = a.residual ? a.b + boff : nullptr;
+#pragma unroll
+  for (int k = 0; k < NBLK; ++k) {
+    T out = 0;
+    if (m[k]) out = a.residual ? b[k * blk + o] - v[k] : v[k];
+    y[k * blk + o] = out;
+  }
+}
+
+template <typename T>
+int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, int batch,
+                 size_t bstride, cudaStream_t st) {
+  ApplyArgs<T> a;
+  a.g = L.g;
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.bstride = bstride;
+  a.residual = residual ? 1 : 0;
+  const bool f64 = sizeof(T) == 8;
+  a.kinv = (const T *)(f64 ? (const void *)L.kinv64 : (const void *)L.kinv32);
+  a.wm = (const T *)(f64 ? (const void *)L.wm64 : (const void *)L.wm32);
+  a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
+  dim3 block(kTX, kTY);
+  dim3 grid((L.g.pitch + kTX - 1) / kTX, (L.n + 1 + kTY - 1) / kTY, batch);
+  const size_t smem = sizeof(T) * 26 * kEX * kEY;
+  BMG_PROF_BEGIN(BMG_PROF_APPLY, L.n, st);
+  if (L.wm_full) {
+    static bool attr = false;
+    if (!attr) {
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    apply_kernel<T, 1><<<grid, block, smem, st>>>(a);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+    apply_kernel<T, 0><<<grid, block, smem, st>>>(a);
+  }
+  BMG_PROF_END(st, (double)L.n * L.n * batch);
+  BMG_CHECK_LAUNCH("apply_kernel");
+  return BMG_OK;
+}
+
+template int launch_apply<double>(const Level &, const double *, const double *, double *, bool,
+                                  int, size_t, cudaStream_t);
+template int launch_apply<float>(const Level &, const float *, const float *, float *, bool, int,
+                                 size_t, cudaStream_t);
+
+// --------------------------------------------------------------------------------------
+// Galerkin coarsening of the RT0 mass (the coarse-level reading for a per-triangle K):
+// Wm_T = sum over the 4 children c of Q_c^T Wm_c Q_c.
+struct CoarsenArgs {
+  Grid gf, gc;
+  const double *kinv_f;   // fine per-triangle K^{-1} (fine_full == 0)
+  const double *wm_f;     // fine 3x3 masses (fine_full == 1)
+  int fine_full;
+  double M1[2][9];        // tau * unit RT0 mass of the fine level
+  double *wm_c64;
+  float *wm_c32;
+  int child_o[2][4], child_di[2][4], child_dj[2][4];
+  double Q[2][4][3][3];
+};
+
+__global__ void coarsen_wmass_kernel(const __grid_constant__ CoarsenArgs a) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nc = a.gc.n;
+  if (I >= nc || J >= nc) return;
+  for (int o = 0; o < 2; ++o) {
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int c = 0; c < 4; ++c) {
+      const int co = a.child_o[o][c];
+      const size_t fo = (size_t)(2 * J + a.child_dj[o][c]) * a.gf.pitch + (2 * I + a.child_di[o][c]);
+      double Mc[3][3];
+      if (a.fine_full) {
+        const double *w = a.wm_f + (size_t)co * 6 * a.gf.blk + fo;
+        const size_t s = a.gf.blk;
+        Mc[0][0] = w[0]; Mc[0][1] = Mc[1][0] = w[s]; Mc[0][2] = Mc[2][0] = w[2 * s];
+        Mc[1][1] = w[3 * s]; Mc[1][2] = Mc[2][1] = w[4 * s]; Mc[2][2] = w[5 * s];
+      } else {
+        const double k = a.kinv_f[(size_t)co * a.gf.blk + fo];
+        for (int r = 0; r < 3; ++r)
+          for (int s = 0; s < 3; ++s) Mc[r][s] = k * a.M1[co][r * 3 + s];
+      }
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+          double acc = 0;
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) acc += a.Q[o][c][p][r] * Mc[p][q] * a.Q[o][c][q][s];
+          M[r][s] += acc;
+        }
+    }
+    const size_t co = (size_t)J * a.gc.pitch + I;
+    const double vals[6] = {M[0][0], 0.5 * (M[0][1] + M[1][0]), 0.5 * (M[0][2] + M[2][0]),
+                            M[1][1], 0.5 * (M[1][2] + M[2][1]), M[2][2]};
+    for (int k = 0; k < 6; ++k) {
+      a.wm_c64[(size_t)(o * 6 + k) * a.gc.blk + co] = vals[k];
+      a.wm_c32[(size_t)(o * 6 + k) * a.gc.blk + co] = (float)vals[k];
+    }
+  }
+}
+
+extern TransferTables g_tables_host;
+
+int launch_coarsen_wmass(const Level &fine, Level &coarse, cudaStream_t st) {
+  CoarsenArgs a;
+  a.gf = fine.g;
+  a.gc = coarse.g;
+  a.kinv_f = fine.kinv64;
+  a.wm_f = fine.wm64;
+  a.fine_full = fine.wm_full ? 1 : 0;
+  for (int o = 0; o < 2; ++o)
+    for (int k = 0; k < 9; ++k) a.M1[o][k] = fine.c64.M1[o][k];
+  a.wm_c64 = coarse.wm64;
+  a.wm_c32 = coarse.wm32;
+  const TransferTables &t = g_tables_host;
+  for (int o = 0; o < 2; ++o)
+    for (int c = 0; c < 4; ++c) {
+      a.child_o[o][c] = t.child_o[o][c];
+      a.child_di[o][c] = t.child_di[o][c];
+      a.child_dj[o][c] = t.child_dj[o][c];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) a.Q[o][c][p][q] = t.Q[o][c][p][q];
+    }
+  dim3 block(16, 16);
+  dim3 grid((coarse.n + 15) / 16, (coarse.n + 15) / 16);
+  coarsen_wmass_kernel<<<grid, block, 0, st>>>(a);
+  BMG_CHECK_LAUNCH("coarsen_wmass_kernel");
+  return BMG_OK;
+}
+
+}  // namespace bmg

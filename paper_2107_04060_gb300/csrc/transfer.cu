@@ -1,0 +1,112 @@
+// Grid transfers (Sec. 3, Eq. block_interp; Sec. 3.1): prolongation-and-correct
+// x_f += P x_c and restriction r_c = P^T r_f, as constant stencils per DoF type (and per
+// parity class of the fine position for P).  The tables are built once on the host from
+// the definitions of P_u (divergence-preserving), P_w (canonical RT0) and P_p (injection);
+// see element.cpp.  Couplings to positions outside the grid are skipped and slots beyond
+// the valid ranges hold zeros, so the interior stencil is exact up to the boundary.
+#include "bmg_internal.h"
+#include "kernels_common.cuh"
+
+namespace bmg {
+
+TransferTables g_tables_host;
+__constant__ StencilEntry c_pro[NBLK][4][kMaxPro];
+__constant__ int c_npro[NBLK][4];
+__constant__ StencilEntry c_res[NBLK][kMaxRes];
+__constant__ int c_nres[NBLK];
+
+int upload_transfer_tables() {
+  static bool done = false;
+  if (done) return BMG_OK;
+  build_transfer_tables(&g_tables_host);
+  BMG_CUDA(cudaMemcpyToSymbol(c_pro, g_tables_host.pro, sizeof(g_tables_host.pro)));
+  BMG_CUDA(cudaMemcpyToSymbol(c_npro, g_tables_host.npro, sizeof(g_tables_host.npro)));
+  BMG_CUDA(cudaMemcpyToSymbol(c_res, g_tables_host.res, sizeof(g_tables_host.res)));
+  BMG_CUDA(cudaMemcpyToSymbol(c_nres, g_tables_host.nres, sizeof(g_tables_host.nres)));
+  done = true;
+  return BMG_OK;
+}
+
+template <typename T>
+__global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nc = gc.n, nf = gf.n;
+  if (I >= gc.pitch || J > nc) return;
+  const size_t o = (size_t)J * gc.pitch + I;
+  if (I > nc) {
+#pragma unroll
+    for (int k = 0; k < NBLK; ++k) rc[k * gc.blk + o] = 0;
+    return;
+  }
+  bool m[NBLK];
+  dof_masks(I, J, nc, m);
+  for (int ct = 0; ct < NBLK; ++ct) {
+    T acc = 0;
+    if (m[ct]) {
+      const int ne = c_nres[ct];
+      for (int e = 0; e < ne; ++e) {
+        const StencilEntry se = c_res[ct][e];
+        const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
+        if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
+        acc += (T)se.coef * rf[se.type * gf.blk + (size_t)fj * gf.pitch + fi];
+      }
+    }
+    rc[ct * gc.blk + o] = acc;
+  }
+}
+
+template <typename T>
+__global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nf = gf.n, nc = gc.n;
+  if (i > nf || j > nf) return;
+  bool m[NBLK];
+  dof_masks(i, j, nf, m);
+  const int par = (i & 1) + 2 * (j & 1);
+  const int I0 = i >> 1, J0 = j >> 1;
+  const size_t o = (size_t)j * gf.pitch + i;
+  for (int t = 0; t < NBLK; ++t) {
+    if (!m[t]) continue;
+    T acc = 0;
+    const int ne = c_npro[t][par];
+    for (int e = 0; e < ne; ++e) {
+      const StencilEntry se = c_pro[t][par][e];
+      const int I = I0 + se.di, J = J0 + se.dj;
+      if (I < 0 || J < 0 || I > nc || J > nc) continue;
+      acc += (T)se.coef * xc[se.type * gc.blk + (size_t)J * gc.pitch + I];
+    }
+    xf[t * gf.blk + o] += acc;
+  }
+}
+
+template <typename T>
+int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, cudaStream_t st) {
+  dim3 block(32, 4);
+  dim3 grid((coarse.g.pitch + 31) / 32, (coarse.n + 1 + 3) / 4);
+  { BMG_PROF_BEGIN(BMG_PROF_RESTRICT, fine.n, st);
+  restrict_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, rf, rc);
+    BMG_PROF_END(st, (double)fine.n * fine.n); }
+  BMG_CHECK_LAUNCH("restrict_kernel");
+  return BMG_OK;
+}
+
+template <typename T>
+int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *xf,
+                       cudaStream_t st) {
+  dim3 block(32, 4);
+  dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4);
+  { BMG_PROF_BEGIN(BMG_PROF_PROLONG, fine.n, st);
+  prolong_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, xc, xf);
+    BMG_PROF_END(st, (double)fine.n * fine.n); }
+  BMG_CHECK_LAUNCH("prolong_kernel");
+  return BMG_OK;
+}
+
+template int launch_restrict<double>(const Level &, const Level &, const double *, double *, cudaStream_t);
+template int launch_restrict<float>(const Level &, const Level &, const float *, float *, cudaStream_t);
+template int launch_prolong_add<double>(const Level &, const Level &, const double *, double *, cudaStream_t);
+template int launch_prolong_add<float>(const Level &, const Level &, const float *, float *, cudaStream_t);
+
+}  // namespace bmg

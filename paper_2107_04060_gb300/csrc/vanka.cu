@@ -1,0 +1,293 @@
+// Additive Vanka relaxation on vertex patches (Sec. 3.2.1, Fig. 3).
+//
+// Patch of vertex v = (i, j), fixed slot order (20 slots):
+//   0, 1      ux, uy at v
+//   2 + e     bubble on incident edge e,  8 + e  RT0 on edge e, e = 0..5:
+//             E0 = h(i,j), E1 = v(i,j), E2 = h(i-1,j), E3 = v(i,j-1), E4 = d(i-1,j), E5 = d(i,j-1)
+//   14 + t    P0 on incident triangle t = 0..5:
+//             L(i,j), L(i-1,j), L(i,j-1), U(i-1,j), U(i-1,j-1), U(i,j-1)
+// The 8-DoF displacement patch (Fig. 3 left, used inside Braess-Sarazin) is slots 0..7 of
+// A_u^RQ.  Slots of DoFs that do not exist or are constrained carry an identity row and
+// column, so every patch is a fixed-size system; their residual entries are zero.
+//
+// Setup: the patch matrix V_l A V_l^T is the sum of the element matrices of the six
+// incident triangles restricted to the patch, inverted in FP64 by Gauss-Jordan with
+// partial pivoting (one thread per distinct patch).  Patches with identical matrices share
+// one inverse ("slot"): with uniform coefficients every interior patch uses slot 0.
+//
+// Sweep: x <- x + omega * sum_l V_l^T D_l (V_l A V_l^T)^{-1} V_l r with the natural weights
+// D_l (1 for a vertex DoF, 1/2 for an edge DoF, 1/3 for a triangle DoF: every edge lies in
+// the patches of its two end points, every triangle in those of its three vertices).
+// One CTA computes the local solves of a 32 x 8 block of patches into shared memory and
+// then gathers the weighted corrections of the 31 x 7 positions whose patches it holds:
+// deterministic, no atomics.
+#include "bmg_internal.h"
+#include "kernels_common.cuh"
+
+namespace bmg {
+
+// incident triangle t: cell offset, orientation, local index of v, local edge -> patch edge
+__constant__ int c_tdi[6] = {0, -1, 0, -1, -1, 0};
+__constant__ int c_tdj[6] = {0, 0, -1, 0, -1, -1};
+__constant__ int c_to[6] = {0, 0, 0, 1, 1, 1};
+__constant__ int c_tlv[6] = {0, 1, 2, 2, 0, 1};
+__constant__ int c_temap[6][3] = {{-1, 1, 0}, {4, -1, 2}, {5, 3, -1},
+                                  {4, 1, -1}, {-1, 3, 2}, {5, -1, 0}};
+
+// Existence / freedom of the 20 patch slots of vertex (vi, vj).
+__device__ __forceinline__ void patch_active(int vi, int vj, int n, bool act[20]) {
+  const bool vf = vfree(vi, vj, n);
+  act[0] = act[1] = vf;
+  const bool ex[6] = {vi < n, vj < n, vi >= 1, vj >= 1, vi >= 1 && vj < n, vi < n && vj >= 1};
+  const bool hfree = vj > 0 && vj < n, vfr = vi > 0 && vi < n;
+  const bool bfree[6] = {hfree, vfr, hfree, vfr, true, true};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    act[2 + e] = ex[e] && bfree[e];
+    act[8 + e] = ex[e];
+  }
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const int ci = vi + c_tdi[t], cj = vj + c_tdj[t];
+    act[14 + t] = ci >= 0 && cj >= 0 && ci < n && cj < n;
+  }
+}
+
+struct VankaSetupArgs {
+  Grid g;
+  const double *kinv;
+  const double *wm;
+  int wm_full;
+  OpCoefs<double> c;
+  double pshift_area;
+  const int *rep_i, *rep_j;
+  int nrep;
+  int psize;
+  double *inv64;
+  float *inv32;
+  int *flag;
+};
+
+__global__ void __launch_bounds__(64) vanka_setup_kernel(const __grid_constant__ VankaSetupArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nrep) return;
+  const int vi = a.rep_i[s], vj = a.rep_j[s];
+  const int n = a.g.n, P = a.g.pitch;
+  const int ps = a.psize;
+  double M[20][20];
+  for (int r = 0; r < 20; ++r)
+    for (int c = 0; c < 20; ++c) M[r][c] = 0.0;
+  bool act[20];
+  patch_active(vi, vj, n, act);
+  for (int t = 0; t < 6; ++t) {
+    if (!act[14 + t]) continue;
+    const int ci = vi + c_tdi[t], cj = vj + c_tdj[t], o = c_to[t], lv = c_tlv[t];
+    const size_t co = (size_t)cj * P + ci;
+    // local DoFs of the triangle that belong to the patch, with their slots
+    int la[7], sl[7], nl = 0;
+    la[nl] = lv; sl[nl++] = 0;
+    la[nl] = 3 + lv; sl[nl++] = 1;
+    for (int e = 0; e < 3; ++e)
+      if (c_temap[t][e] >= 0) { la[nl] = 6 + e; sl[nl++] = 2 + c_temap[t][e]; }
+    const int nu = nl;
+    if (ps == 20) {
+      for (int e = 0; e < 3; ++e)
+        if (c_temap[t][e] >= 0) { la[nl] = 9 + e; sl[nl++] = 8 + c_temap[t][e]; }
+      la[nl] = 12; sl[nl++] = 14 + t;
+    }
+    double W[3][3];
+    if (a.wm_full) {
+      const double *w = a.wm + (size_t)o * 6 * a.g.blk + co;
+      const size_t b = a.g.blk;
+      W[0][0] = w[0]; W[0][1] = W[1][0] = w[b]; W[0][2] = W[2][0] = w[2 * b];
+      W[1][1] = w[3 * b]; W[1][2] = W[2][1] = w[4 * b]; W[2][2] = w[5 * b];
+    } else {
+      const double k = a.kinv[(size_t)o * a.g.blk + co];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) W[r][c] = k * a.c.M1[o][r * 3 + c];
+    }
+    for (int p = 0; p < nl; ++p)
+      for (int q = 0; q < nl; ++q) {
+        const int A = la[p], B = la[q];
+        double v = 0.0;
+        if (A < 9 && B < 9) v = a.c.A[o][A * 9 + B] + a.c.lam_area * a.c.g[o][A] * a.c.g[o][B];
+        else if (A < 9 && B == 12) v = -a.c.alpha * a.c.g[o][A];
+        else if (A == 12 && B < 9) v = -a.c.alpha * a.c.g[o][B];
+        else if (A >= 9 && A < 12 && B >= 9 && B < 12) v = W[A - 9][B - 9];
+        else if (A >= 9 && A < 12 && B == 12) v = -a.c.dw[o][A - 9];
+        else if (A == 12 && B >= 9 && B < 12) v = -a.c.dw[o][B - 9];
+        else if (A == 12 && B == 12) v = -a.c.pp - a.pshift_area;
+        M[sl[p]][sl[q]] += v;
+      }
+    (void)nu;
+  }
+  double mmax = 0.0;
+  for (int r = 0; r < ps; ++r) {
+    if (!act[r]) {
+      for (int c = 0; c < ps; ++c) M[r][c] = M[c][r] = 0.0;
+      M[r][r] = 1.0;
+    }
+  }
+  for (int r = 0; r < ps; ++r)
+    for (int c = 0; c < ps; ++c) mmax = fmax(mmax, fabs(M[r][c]));
+  // Gauss-Jordan with partial pivoting on [M | I]
+  double Inv[20][20];
+  for (int r = 0; r < ps; ++r)
+    for (int c = 0; c < ps; ++c) Inv[r][c] = (r == c) ? 1.0 : 0.0;
+  bool ok = true;
+  for (int k = 0; k < ps; ++k) {
+    int piv = k;
+    double best = fabs(M[k][k]);
+    for (int r = k + 1; r < ps; ++r)
+      if (fabs(M[r][k]) > best) { best = fabs(M[r][k]); piv = r; }
+    if (!(best > 1e-15 * mmax)) { ok = false; break; }
+    if (piv != k)
+      for (int c = 0; c < ps; ++c) {
+        double t = M[k][c]; M[k][c] = M[piv][c]; M[piv][c] = t;
+        t = Inv[k][c]; Inv[k][c] = Inv[piv][c]; Inv[piv][c] = t;
+      }
+    const double d = 1.0 / M[k][k];
+    for (int c = 0; c < ps; ++c) { M[k][c] *= d; Inv[k][c] *= d; }
+    for (int r = 0; r < ps; ++r) {
+      if (r == k) continue;
+      const double f = M[r][k];
+      if (f == 0.0) continue;
+      for (int c = 0; c < ps; ++c) { M[r][c] -= f * M[k][c]; Inv[r][c] -= f * Inv[k][c]; }
+    }
+  }
+  if (!ok) atomicOr(a.flag, 1);
+  for (int r = 0; r < ps; ++r)
+    for (int c = 0; c < ps; ++c) {
+      const double v = ok ? Inv[r][c] : 0.0;
+      a.inv64[(size_t)(r * ps + c) * a.nrep + s] = v;
+      a.inv32[(size_t)(r * ps + c) * a.nrep + s] = (float)v;
+    }
+}
+
+int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
+                       double p_shift_area, int psize, int *d_flag, cudaStream_t st) {
+  VankaSetupArgs a;
+  a.g = L.g;
+  a.kinv = L.kinv64;
+  a.wm = L.wm64;
+  a.wm_full = L.wm_full ? 1 : 0;
+  a.c = L.c64;
+  a.pshift_area = p_shift_area;
+  a.rep_i = rep_i;
+  a.rep_j = rep_j;
+  a.nrep = nrep;
+  a.psize = psize;
+  a.inv64 = L.pinv64;
+  a.inv32 = L.pinv32;
+  a.flag = d_flag;
+  vanka_setup_kernel<<<(nrep + 63) / 64, 64, 0, st>>>(a);
+  BMG_CHECK_LAUNCH("vanka_setup_kernel");
+  return BMG_OK;
+}
+
+// --------------------------------------------------------------------------------------
+constexpr int kPX = 32, kPY = 8;   // patches per CTA; outputs per CTA: 31 x 7
+
+template <typename T>
+struct VankaSweepArgs {
+  Grid g;
+  const T *r;
+  T *x;
+  const int *slot;
+  const T *inv;
+  int nslots;
+  T omega;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kPX *kPY) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+  __shared__ T sx[kPX * kPY][20];
+  const int n = a.g.n, P = a.g.pitch;
+  const size_t blk = a.g.blk;
+  const int i0 = blockIdx.x * (kPX - 1), j0 = blockIdx.y * (kPY - 1);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
+  {
+    const int pi = i0 + tx, pj = j0 + ty;
+    if (pi <= n && pj <= n) {
+      const T *r = a.r;
+      const size_t o = (size_t)pj * P + pi;
+      T rl[20];
+      rl[0] = r[UX * blk + o];
+      rl[1] = r[UY * blk + o];
+      // E0 = h(pi,pj), E1 = v(pi,pj) (slots beyond the grid hold zeros)
+      rl[2] = r[BH * blk + o];
+      rl[8] = r[WH * blk + o];
+      rl[3] = r[BV * blk + o];
+      rl[9] = r[WV * blk + o];
+      const bool li = pi >= 1, lj = pj >= 1;
+      rl[4] = li ? r[BH * blk + o - 1] : T(0);          // E2 = h(pi-1,pj)
+      rl[10] = li ? r[WH * blk + o - 1] : T(0);
+      rl[5] = lj ? r[BV * blk + o - P] : T(0);          // E3 = v(pi,pj-1)
+      rl[11] = lj ? r[WV * blk + o - P] : T(0);
+      rl[6] = li ? r[BD * blk + o - 1] : T(0);          // E4 = d(pi-1,pj)
+      rl[12] = li ? r[WD * blk + o - 1] : T(0);
+      rl[7] = lj ? r[BD * blk + o - P] : T(0);          // E5 = d(pi,pj-1)
+      rl[13] = lj ? r[WD * blk + o - P] : T(0);
+      rl[14] = r[PL * blk + o];                         // L(pi,pj)
+      rl[15] = li ? r[PL * blk + o - 1] : T(0);         // L(pi-1,pj)
+      rl[16] = lj ? r[PL * blk + o - P] : T(0);         // L(pi,pj-1)
+      rl[17] = li ? r[PU * blk + o - 1] : T(0);         // U(pi-1,pj)
+      rl[18] = (li && lj) ? r[PU * blk + o - P - 1] : T(0);   // U(pi-1,pj-1)
+      rl[19] = lj ? r[PU * blk + o - P] : T(0);         // U(pi,pj-1)
+      const int s = a.slot[(size_t)pj * (n + 1) + pi];
+      const T *inv = a.inv + s;
+      const size_t ld = (size_t)a.nslots;
+#pragma unroll
+      for (int row = 0; row < 20; ++row) {
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)(row * 20 + c) * ld], rl[c], acc);
+        sx[tid][row] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  if (tx >= kPX - 1 || ty >= kPY - 1) return;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i > n || j > n) return;
+  auto X = [&](int pi, int pj, int k) -> T { return sx[(pj - j0) * kPX + (pi - i0)][k]; };
+  bool m[NBLK];
+  dof_masks(i, j, n, m);
+  T *x = a.x;
+  const size_t o = (size_t)j * P + i;
+  const T w = a.omega, half = T(0.5) * a.omega, third = a.omega / T(3);
+  if (m[UX]) x[UX * blk + o] += w * X(i, j, 0);
+  if (m[UY]) x[UY * blk + o] += w * X(i, j, 1);
+  if (m[BH]) x[BH * blk + o] += half * (X(i, j, 2) + X(i + 1, j, 4));
+  if (m[BV]) x[BV * blk + o] += half * (X(i, j, 3) + X(i, j + 1, 5));
+  if (m[BD]) x[BD * blk + o] += half * (X(i, j + 1, 7) + X(i + 1, j, 6));
+  if (m[WH]) x[WH * blk + o] += half * (X(i, j, 8) + X(i + 1, j, 10));
+  if (m[WV]) x[WV * blk + o] += half * (X(i, j, 9) + X(i, j + 1, 11));
+  if (m[WD]) x[WD * blk + o] += half * (X(i, j + 1, 13) + X(i + 1, j, 12));
+  if (m[PL]) x[PL * blk + o] += third * (X(i, j, 14) + X(i + 1, j, 15) + X(i, j + 1, 16));
+  if (m[PU]) x[PU * blk + o] += third * (X(i + 1, j + 1, 18) + X(i, j + 1, 19) + X(i + 1, j, 17));
+}
+
+template <typename T>
+int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st) {
+  VankaSweepArgs<T> a;
+  a.g = L.g;
+  a.r = r;
+  a.x = x;
+  a.slot = L.slot;
+  a.inv = (const T *)(sizeof(T) == 8 ? (const void *)L.pinv64 : (const void *)L.pinv32);
+  a.nslots = L.nslots;
+  a.omega = omega;
+  dim3 block(kPX, kPY);
+  dim3 grid((L.n + 1 + kPX - 2) / (kPX - 1), (L.n + 1 + kPY - 2) / (kPY - 1));
+  { BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
+  vanka_sweep_kernel<T><<<grid, block, 0, st>>>(a);
+    BMG_PROF_END(st, (double)L.n * L.n); }
+  BMG_CHECK_LAUNCH("vanka_sweep_kernel");
+  return BMG_OK;
+}
+
+template int launch_vanka_sweep<double>(const Level &, const double *, double *, double, cudaStream_t);
+template int launch_vanka_sweep<float>(const Level &, const float *, float *, float, cudaStream_t);
+
+}  // namespace bmg

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances (all relative to the max-norm of the oracle's result):
+  * FP64 operator application: 1e-12 (the bound stated for FP64 operator applications).
+  * FP64 V-cycle: 1e-9.  Both sides apply the same linear map in FP64 with different
+    summation orders; the exactly inverted Vanka patch matrices have condition numbers up to
+    ~1e5 for these parameters, so rounding differences of ~1e-16 grow to ~1e-11; the margin
+    covers the coarse-level inverses as well.
+  * FGMRES: the same 1e-8 true relative residual, iteration counts within +-1, and the two
+    solutions within 1e-6 relative (both solve to 1e-8 relative residual; the operator's
+    condition number amplifies the residual difference).  At lambda/mu = 1e6 the Arnoldi
+    estimate and the true residual separate near 1e-7 on both sides (FP64 rounding of the
+    lambda B_u^T M_p^{-1} B_u term, amplified by the preconditioner's transient), so the final
+    restart cycle is decided by rounding: there the counts are compared within +-3.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import fem, krylov, mg
+from oracle.mesh import Mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bmg():
+    import torch
+    import paper_2107_04060_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def dev(bmg, n, fields):
+    import torch
+    return torch.from_numpy(bmg.pack(n, fields)).cuda()
+
+
+def to_oracle(bmg, mesh, t):
+    return mesh.pack(bmg.unpack(mesh.n, t.double().cpu().numpy()))
+
+
+def kfield(bmg, n, kL, kU):
+    import torch
+    return torch.from_numpy(bmg.pack_k(n, kL, kU)).cuda()
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+PARAMS = [dict(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0),
+          dict(lam=1e4, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0),
+          dict(lam=1e6, mu=1.3, tau=0.5, alpha=0.8, inv_M=0.0)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 31, 33, 64, 100])
+@pytest.mark.parametrize("pi", [0, 1, 2])
+def test_apply_parity(bmg, n, pi):
+    import torch
+    p = PARAMS[pi]
+    kL, kU = synthetic.lognormal_k(n, 1.5, 10 + n)
+    s = bmg.assemble(n, p["lam"], p["mu"], kfield(bmg, n, kL, kU), 0.0, p["tau"], p["alpha"], p["inv_M"])
+    f = synthetic.uniform_field(n, 20 + n)
+    x = dev(bmg, n, f)
+    y = torch.full_like(x, float("nan"))
+    s.apply(x, y)
+    m = Mesh(n)
+    A = fem.assemble(m, fem.Params(**p), 1 / kL, 1 / kU)
+    yo = A @ m.pack(f)
+    yg = y.cpu().numpy()
+    assert np.isfinite(yg).all()                              # every slot written
+    assert relmax(to_oracle(bmg, m, y), yo) < 1e-12
+    # unused slots are written as zero
+    assert np.count_nonzero(yg) <= len(yo)
+    # residual mode
+    b = dev(bmg, n, synthetic.rhs(n, 30 + n))
+    r = torch.empty_like(x)
+    s.residual(b, x, r)
+    ro = m.pack(synthetic.rhs(n, 30 + n)) - yo
+    assert relmax(to_oracle(bmg, m, r), ro) < 1e-12
+
+
+def test_apply_uniform_k_and_garbage_in_constrained_slots(bmg):
+    import torch
+    n = 40
+    p = PARAMS[1]
+    s = bmg.assemble(n, p["lam"], p["mu"], None, 0.25, p["tau"], p["alpha"], p["inv_M"])
+    f = synthetic.uniform_field(n, 3)
+    x = dev(bmg, n, f)
+    xg = x.clone().view(10, n + 1, bmg.pitch(n))
+    xg[0, 0, :n + 1] = 7.0                       # ux on y = 0 (constrained)
+    xg[2, n, :n] = -3.0                          # bh on y = 1 (constrained)
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    s.apply(x, y1)
+    s.apply(xg.reshape(-1).contiguous(), y2)
+    assert torch.equal(y1, y2)
+    m = Mesh(n)
+    A = fem.assemble(m, fem.Params(**p), np.full((n, n), 4.0), np.full((n, n), 4.0))
+    assert relmax(to_oracle(bmg, m, y1), A @ m.pack(f)) < 1e-12
+
+
+def test_apply_sampled_rows_full_size(bmg):
+    """The bench's 512 x 512 grid, lognormal K: sampled rows computed one by one."""
+    import torch
+    n = 512
+    p = PARAMS[1]
+    kL, kU = synthetic.lognormal_k(n, 2.0, 7)
+    s = bmg.assemble(n, p["lam"], p["mu"], kfield(bmg, n, kL, kU), 0.0, p["tau"], p["alpha"], p["inv_M"])
+    f = synthetic.uniform_field(n, 8)
+    x = dev(bmg, n, f)
+    y = torch.empty_like(x)
+    s.apply(x, y)
+    m = Mesh(n)
+    yg = to_oracle(bmg, m, y)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(m.ndof, 600, replace=False)
+    edge = [m.idx("ux", 1, 1), m.idx("wh", n - 1, n), m.idx("wv", n, n - 1), m.idx("pU", n - 1, n - 1),
+            m.idx("bd", 0, 0), m.idx("bv", 1, n - 1)]
+    rows = np.concatenate([rows, edge])
+    yo = fem.apply_rows(m, fem.Params(**p), 1 / kL, 1 / kU, m.pack(f), rows)
+    scale = np.abs(yo).max()
+    assert np.abs(yg[rows] - yo).max() < 1e-12 * scale
+
+
+def hierarchies(bmg, n, p, kL, kU, smoother, omega, precision="fp64", nu=1):
+    import torch
+    Kf = None if kL is None else kfield(bmg, n, kL, kU)
+    s = bmg.assemble(n, p["lam"], p["mu"], Kf, 1.0, p["tau"], p["alpha"], p["inv_M"])
+    h = bmg.setup_hierarchy(s, smoother, nu, nu, omega=omega, omega_J=1.0, n_coarse=8,
+                            precision=precision)
+    kinvL = np.ones((n, n)) if kL is None else 1 / kL
+    kinvU = np.ones((n, n)) if kU is None else 1 / kU
+    H = mg.Hierarchy(n, fem.Params(**p), kinvL, kinvU, smoother=smoother, omega=omega,
+                     omega_J=1.0, nu1=nu, nu2=nu, n_coarse=8)
+    return s, h, H
+
+
+@pytest.mark.parametrize("n", [16, 32])
+@pytest.mark.parametrize("smoother,omega", [("vanka", 0.8), ("bsr", 0.7)])
+@pytest.mark.parametrize("kind", ["const", "lognormal"])
+def test_vcycle_parity(bmg, n, smoother, omega, kind):
+    import torch
+    p = PARAMS[0] if kind == "const" else PARAMS[1]
+    kL, kU = (None, None) if kind == "const" else synthetic.lognormal_k(n, 1.0, 3)
+    s, h, H = hierarchies(bmg, n, p, kL, kU, smoother, omega)
+    f = synthetic.rhs(n, 5)
+    r = dev(bmg, n, f)
+    z = torch.empty_like(r)
+    h.vcycle(r, z)
+    zo = H.vcycle(H.levels[0].mesh.pack(f))
+    assert relmax(to_oracle(bmg, H.levels[0].mesh, z), zo) < 1e-9
+
+
+@pytest.mark.parametrize("lam,K", [(1.0, 1.0), (1e4, 1e-6), (1e6, 1.0)])
+@pytest.mark.parametrize("smoother,omega", [("vanka", 0.7), ("bsr", 0.7)])
+def test_fgmres_parity(bmg, lam, K, smoother, omega):
+    import torch
+    n = 32
+    p = dict(lam=lam, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    kL, kU = synthetic.constant_k(n, K)
+    s = bmg.assemble(n, lam, 1.0, None, K, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8)
+    H = mg.Hierarchy(n, fem.Params(**p), 1 / kL, 1 / kU, smoother=smoother, omega=omega,
+                     omega_J=1.0, n_coarse=8)
+    f = synthetic.rhs(n, 0)
+    b = dev(bmg, n, f)
+    x = torch.zeros_like(b)
+    info = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=300)
+    A = H.levels[0].A
+    bo = H.levels[0].mesh.pack(f)
+    xo, oinfo = krylov.fgmres(A, bo, H.vcycle, rtol=1e-8, restart=50, maxit=300)
+    assert info["status"] == "converged" and oinfo["converged"]
+    assert info["relres"] <= 1e-8
+    tol_it = 3 if lam >= 1e6 else 1
+    assert abs(info["iters"] - oinfo["iters"]) <= tol_it, (info["iters"], oinfo["iters"])
+    xg = to_oracle(bmg, H.levels[0].mesh, x)
+    assert np.linalg.norm(bo - A @ xg) <= 1e-8 * np.linalg.norm(bo) * 1.0001
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_fp32_vcycle_solves_to_fp64_accuracy(bmg):
+    import torch
+    n = 64
+    p = PARAMS[1]
+    kL, kU = synthetic.lognormal_k(n, 2.0, 11)
+    Kf = kfield(bmg, n, kL, kU)
+    s = bmg.assemble(n, p["lam"], p["mu"], Kf, 0.0, p["tau"], p["alpha"], p["inv_M"])
+    h64 = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, n_coarse=8, precision="fp64")
+    h32 = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, n_coarse=8, precision="fp32")
+    b = dev(bmg, n, synthetic.rhs(n, 1))
+    x64, x32 = torch.zeros_like(b), torch.zeros_like(b)
+    i64 = h64.fgmres_solve(b, x64, rtol=1e-8, maxit=400)
+    i32 = h32.fgmres_solve(b, x32, rtol=1e-8, maxit=400)
+    assert i64["status"] == "converged" and i32["status"] == "converged"
+    assert i32["relres"] <= 1e-8
+    assert i32["iters"] <= i64["iters"] + 5
+    assert (torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)).item() < 1e-5
+
+
+def test_host_buffer_solve_matches_device_solve(bmg):
+    import torch
+    n = 16
+    s = bmg.assemble(n, 1.0, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.8)
+    bh = bmg.pack(n, synthetic.rhs(n, 0))
+    xh = np.zeros_like(bh)
+    ih = h.fgmres_solve_host(bh, xh)
+    b = torch.from_numpy(bh).cuda()
+    x = torch.zeros_like(b)
+    idv = h.fgmres_solve(b, x)
+    assert ih["iters"] == idv["iters"]
+    assert np.array_equal(xh, x.cpu().numpy())
+
+
+def test_deterministic(bmg):
+    import torch
+    n = 32
+    s = bmg.assemble(n, 1e4, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7)
+    b = dev(bmg, n, synthetic.rhs(n, 2))
+    z1, z2 = torch.empty_like(b), torch.empty_like(b)
+    h.vcycle(b, z1)
+    h.vcycle(b, z2)
+    assert torch.equal(z1, z2)
+
+
+def test_error_codes(bmg):
+    import torch
+    with pytest.raises(bmg.BmgError, match="invalid argument"):
+        bmg.assemble(0, 1.0, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    with pytest.raises(bmg.BmgError, match="invalid argument"):
+        bmg.assemble(8, 1.0, 1.0, None, -1.0, 1.0, 1.0, 1.0)
+    n = 8
+    kL, kU = synthetic.constant_k(n, 1.0)
+    kL[3, 4] = -2.0
+    with pytest.raises(bmg.BmgError, match="non-finite or non-positive"):
+        bmg.assemble(n, 1.0, 1.0, kfield(bmg, n, kL, kU), 0.0, 1.0, 1.0, 1.0)
+    s = bmg.assemble(24, 1.0, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    with pytest.raises(bmg.BmgError, match="invalid argument"):
+        bmg.setup_hierarchy(s, "vanka", 1, 1, n_coarse=16)        # 24 / 16 not a power of 2
+    s = bmg.assemble(16, 1.0, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1)
+    b = torch.zeros(bmg.vector_len(16), dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    info = h.fgmres_solve(b, x)                                   # zero right-hand side
+    assert info["status"] == "converged" and float(x.abs().max()) == 0.0
+    b[0:5] = float("nan")
+    with pytest.raises(bmg.BmgError, match="non-finite"):
+        h.fgmres_solve(b, x)
