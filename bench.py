@@ -1,0 +1,359 @@
+"""Benchmark: MDOF/s to a 1e-8 relative residual for FGMRES preconditioned by the monolithic
+multigrid V-cycle on the reduced-quadrature Biot system, FP64 V-cycle vs FP32 V-cycle.
+
+Workload (one step): the 512 x 512 triangulated unit square (2,619,394 free DoFs), the
+parameter sweep lambda in {1, 1e4, 1e6} x K in {1, 1e-6} with mu = tau = alpha = 1, 1/M = 1,
+right-hand side uniform in [-1, 1] on the free DoFs (seeds 0..5, one per parameter pair),
+each solved with a Vanka V(1,1) and an inexact Braess-Sarazin V(1,1) preconditioner:
+12 plain FP64 solves.  A second arm ("fp32_mg") times the 8 solves with lambda <= 1e4 with
+FP32 V-cycles inside FP64 FGMRES against the same 8 solves with FP64 V-cycles (at
+lambda/mu = 1e6 an FP32 V-cycle cannot converge: FP32 rounding of a nearly divergence-free
+displacement, times lambda, is a 6% error in the grad-div term).  Setup (assembly, hierarchy, factorisations) is outside the
+timed region; every input is resident in HBM when it starts.  L2 (129 MB) is flushed by a
+256 MB write between solves.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): replicas only -- every rank runs the whole workload on its own GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LAMBDAS = (1.0, 1e4, 1e6)
+KS = (1.0, 1e-6)
+INV_M = 1.0
+N_GRID = 512
+RTOL = 1e-8
+RESTART = 50
+MAXIT = 1000
+# roofline denominators: FP64 FMA pipe (nominal 1.25 TFLOP/s for the GB300; measured
+# 1.20 TFLOP/s with a register FMA loop), HBM from the driver-written measured peaks
+FP64_PEAK_TFLOPS = 1.25
+# algorithmic work per grid cell of the fine-level kernels (derivation in the design doc)
+FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 244 + 26, "vanka_u": 2 * 64 + 10}
+BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208}
+
+
+def smoother_cases():
+    cases = []
+    for li, lam in enumerate(LAMBDAS):
+        for ki, K in enumerate(KS):
+            seed = li * len(KS) + ki
+            cases.append(dict(lam=lam, K=K, seed=seed, smoother="vanka", omega=0.8 if lam == 1.0 else 0.7))
+            cases.append(dict(lam=lam, K=K, seed=seed, smoother="bsr", omega=0.7))
+    return cases
+
+
+# ----------------------------------------------------------------------------------------
+def clocks_sampler(stop_evt, out):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+           "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits"]
+    while not stop_evt.is_set():
+        try:
+            line = subprocess.run(cmd, capture_output=True, text=True, timeout=5).stdout.strip()
+            if line:
+                out.append(line.splitlines()[0])
+        except Exception:
+            pass
+        stop_evt.wait(0.2)
+
+
+def summarize_clocks(lines):
+    import statistics
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        p = [x.strip() for x in ln.split(",")]
+        try:
+            sm.append(float(p[1]))
+            mx.append(float(p[2]))
+        except (ValueError, IndexError):
+            continue
+        for nm, v in zip(names, p[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+def oracle_sample(n: int, cases) -> dict:
+    """Time the CPU oracle (as it stands) on the same 12 solves on an n x n grid; runs in a
+    child process with one BLAS / OpenMP thread."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+import synthetic
+from oracle import fem, mg, krylov
+n = %d
+cases = json.loads(%r)
+tot, dofs, its = 0.0, 0, []
+for c in cases:
+    prm = fem.Params(lam=c["lam"], mu=1.0, tau=1.0, alpha=1.0, inv_M=%r)
+    kL, kU = synthetic.constant_k(n, c["K"])
+    H = mg.Hierarchy(n, prm, 1 / kL, 1 / kU, smoother=c["smoother"], omega=c["omega"], omega_J=1.0)
+    L = H.levels[0]
+    b = L.mesh.pack(synthetic.rhs(n, c["seed"]))
+    t = time.perf_counter()
+    x, info = krylov.fgmres(L.A, b, H.vcycle, rtol=%r, restart=%d, maxit=%d)
+    tot += time.perf_counter() - t
+    dofs += len(L.mesh.free_idx)
+    its.append(info["iters"])
+print(json.dumps(dict(seconds=tot, dofs=dofs, iters=its)))
+""" % (ROOT, n, json.dumps(cases), INV_M, RTOL, RESTART, MAXIT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               PYTHONPATH=ROOT)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + p.stderr[-2000:])
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    r["mdofs"] = r["dofs"] / r["seconds"] / 1e6
+    return r
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed on this host (rank 0 only)."""
+    if rank != 0:
+        return
+    n = 64
+    cases = smoother_cases()
+    t_steps = []
+    last = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(n, cases)
+        if s >= args.warmup:
+            t_steps.append(r["seconds"])
+        last = r
+    sec = sum(t_steps) / len(t_steps)
+    value = last["dofs"] / sec / 1e6
+    sample = (f"the 12 solves of the workload (same parameters, smoothers, seeds, tolerance) on a "
+              f"{n}x{n} grid ({last['dofs'] // 12} free DoFs each) instead of 512x512; solve time only")
+    out = {"metric": "MDOF/s to 1e-8 rel. residual (FGMRES + monolithic MG V(1,1))", "value": value,
+           "unit": "MDOF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"biot-rq 512x512 sweep (sampled on {n}x{n})", "n": n,
+                      "solves_per_step": 12, "iters": last["iters"]},
+           "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    st = torch.cuda.current_stream()
+    n = args.n
+    nfree = bmg.free_dofs(n)
+    cases = smoother_cases()
+
+    # ---- setup (outside the timed region)
+    systems, work = {}, []
+    for c in cases:
+        key = (c["lam"], c["K"])
+        if key not in systems:
+            systems[key] = bmg.assemble(n, c["lam"], 1.0, None, c["K"], 1.0, 1.0, INV_M)
+    rhs = {}
+    for c in cases:
+        if c["seed"] not in rhs:
+            rhs[c["seed"]] = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, c["seed"]))).to(dev)
+    precisions = ["fp64"] + ([] if args.no_fp32 else ["fp32"])
+    fp32_cases = [ci for ci, c in enumerate(cases) if c["lam"] <= 1e4]
+    hier = {}
+    t0 = time.perf_counter()
+    for prec in precisions:
+        for ci, c in enumerate(cases):
+            if prec == "fp32" and ci not in fp32_cases:
+                continue
+            hier[prec, ci] = bmg.setup_hierarchy(systems[c["lam"], c["K"]], c["smoother"], 1, 1,
+                                                 omega=c["omega"], omega_J=1.0, n_coarse=8,
+                                                 precision=prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    x = torch.zeros(bmg.vector_len(n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(prec, record=None, subset=None):
+        for ci, c in enumerate(cases):
+            if subset is not None and ci not in subset:
+                continue
+            flush.fill_(float(ci))
+            info = hier[prec, ci].fgmres_solve(rhs[c["seed"]], x, rtol=RTOL, restart=RESTART,
+                                               maxit=MAXIT, x0_is_zero=True)
+            if info["status"] != "converged":
+                raise RuntimeError(f"solve did not converge: {c} {info}")
+            if record is not None:
+                record.append((c, info))
+
+    def timed(prec, steps, profile=None, subset=None):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        recs = []
+        barrier()
+        l0 = bmg.launch_count()
+        if profile:
+            bmg.profile_start(profile, n)
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(st)
+        for _ in range(steps):
+            one_step(prec, recs, subset)
+        ev1.record(st)
+        torch.cuda.nvtx.range_pop()
+        barrier()
+        prof = bmg.profile_stop() if profile else None
+        launches = bmg.launch_count() - l0
+        ms = ev0.elapsed_time(ev1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, recs, prof, launches
+
+    # ---- warm-up; the warm-up also decides which kernel family dominates (fine level)
+    for prec in precisions:
+        for _ in range(args.warmup):
+            one_step(prec, subset=None if prec == "fp64" else fp32_cases)
+    shares = {}
+    for fam in ("vanka", "apply", "vanka_u"):
+        bmg.profile_start(fam, n)
+        one_step("fp64")
+        torch.cuda.synchronize()
+        shares[fam] = bmg.profile_stop()
+    dominant = max(shares, key=lambda k: shares[k]["ms"])
+
+    # ---- timed region (FP64 V-cycle), clocks sampled meanwhile
+    samples, stop = [], threading.Event()
+    th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
+    th.start()
+    ms64, recs64, prof, launches = timed("fp64", args.steps, profile=dominant)
+    ms32 = None
+    if "fp32" in precisions:
+        ms32, recs32, _, _ = timed("fp32", args.steps, subset=fp32_cases)
+        ms64s, _, _, _ = timed("fp64", args.steps, subset=fp32_cases)
+    stop.set()
+    th.join(timeout=5)
+    clocks = summarize_clocks(samples)
+
+    # ---- end to end through the host-buffer entry point (FP64 arm)
+    hb = {s: torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory() for s in rhs}
+    for s in rhs:
+        hb[s].copy_(rhs[s].cpu())
+    hx = torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for ci, c in enumerate(cases):
+            hier["fp64", ci].fgmres_solve_host(hb[c["seed"]].numpy(), hx.numpy(), rtol=RTOL,
+                                                restart=RESTART, maxit=MAXIT)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    vec_bytes = bmg.vector_len(n) * 8
+
+    work_dofs = len(cases) * nfree * world
+    value = work_dofs / (ms64 * 1e-3) / 1e6
+    out = {
+        "metric": "MDOF/s to 1e-8 rel. residual (FGMRES + monolithic MG V(1,1))",
+        "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"biot-rq {n}x{n} sweep: lambda {list(LAMBDAS)} x K {list(KS)}, "
+                               f"Vanka + BSR V(1,1), 12 FP64 solves to 1e-8",
+                   "n": n, "free_dofs": nfree, "solves_per_step": len(cases), "inv_M": INV_M,
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between solves",
+                   "iters": [r[1]["iters"] for r in recs64[:len(cases)]],
+                   "setup_s": round(setup_s, 3)},
+        "gpu_launches": launches,
+        "e2e": {"value": work_dofs / (e2e_ms * 1e-3) / 1e6, "unit": "MDOF/s",
+                "h2d_bytes_per_step": len(cases) * vec_bytes, "d2h_bytes_per_step": len(cases) * vec_bytes},
+        "clocks": clocks,
+    }
+    if ms32 is not None:
+        sub_dofs = len(fp32_cases) * nfree * world
+        out["fp32_mg"] = {"workload": "the 8 solves with lambda <= 1e4", "value": sub_dofs / (ms32 * 1e-3) / 1e6,
+                          "unit": "MDOF/s", "ms_per_step": ms32,
+                          "fp64_same_solves": {"value": sub_dofs / (ms64s * 1e-3) / 1e6, "ms_per_step": ms64s},
+                          "speedup_vs_fp64": ms64s / ms32,
+                          "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]]}
+    if prof and prof["launches"]:
+        avg_ms = prof["ms"] / prof["launches"]
+        cells = prof["cells"] / prof["launches"]
+        flops = FLOPS_PER_CELL[dominant] * cells
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        out["roofline"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
+                           "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                           "avg_launch_ms": avg_ms, "launches": prof["launches"],
+                           "peak_source": "nominal FP64 rate (derivation in DESIGN.md)",
+                           "shares_ms": {k: round(v["ms"], 3) for k, v in shares.items()}}
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r = oracle_sample(64, cases)
+            out["cpu_baseline"] = {"value": r["mdofs"], "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                                   "sample": "the 12 solves of this workload on a 64x64 grid "
+                                             f"({r['dofs'] // 12} free DoFs each), solve time only, "
+                                             f"{r['seconds']:.1f} s"}
+        except Exception as e:  # reported, never silently replaced
+            out["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    if args.verbose:
+        for c, info in recs64[:len(cases)]:
+            print("fp64", c, info, file=sys.stderr)
+        if ms32 is not None:
+            for c, info in recs32[:len(fp32_cases)]:
+                print("fp32", c, info, file=sys.stderr)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

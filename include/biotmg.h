@@ -189,6 +189,8 @@ int bmg_fgmres_solve_host(bmg_hierarchy *h, const double *b_host, double *x_host
 #define BMG_PROF_COARSE 6     /* coarsest-grid solve                                   */
 #define BMG_PROF_KRYLOV 7     /* FGMRES vector kernels (dots, updates, scaling)         */
 int bmg_profile_start(int kernel, int n);
+/* Number of kernels this library has launched in the process so far (host-side count). */
+long long bmg_launch_count(void);
 int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
 /* Grid size of a system / hierarchy (cells per side). */

@@ -4,7 +4,7 @@ reduced-quadrature three-field Biot system (arXiv 2107.04060).
 The binding only marshals arguments: every step of assembly, relaxation, transfer, coarse
 solve and Krylov iteration runs in the library's CUDA kernels.  PyTorch provides device
 memory and streams.  There is no CPU fallback: importing this package fails if the shared
-library has not been built (``python -m paper_2107_04060_gb300.build``), and every call
+library has not been built (``python paper_2107_04060_gb300/build.py``), and every call
 fails if no CUDA device is usable.
 
 Names follow the C ABI of ``include/biotmg.h``: ``assemble``, ``setup_hierarchy``,
@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbiotmg.so")
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2107_04060_gb300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2107_04060_gb300/build.py` "
                       "(there is no CPU fallback)")
 lib = C.CDLL(LIB_PATH)
 
@@ -66,6 +66,7 @@ _sig = {
     "bmg_destroy_hierarchy": (None, [_vp]),
     "bmg_status_string": (C.c_char_p, [C.c_int]),
     "bmg_profile_start": (C.c_int, [C.c_int, C.c_int]),
+    "bmg_launch_count": (C.c_longlong, []),
     "bmg_profile_stop": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "bmg_last_error": (C.c_char_p, []),
 }
@@ -258,6 +259,11 @@ def vcycle(h: Hierarchy, r, z, stream=None):
 
 
 PROF = {"apply": 1, "vanka": 2, "vanka_u": 3, "restrict": 4, "prolong": 5, "coarse": 6, "krylov": 7}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return lib.bmg_launch_count()
 
 
 def profile_start(kernel: str, n: int = 0):

@@ -13,6 +13,7 @@
 namespace bmg {
 
 static thread_local std::string g_last_error;
+long long g_launches = 0;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -99,6 +100,8 @@ void prof_end(cudaStream_t st, double cells) {
 }  // namespace bmg
 
 using namespace bmg;
+
+extern "C" long long bmg_launch_count(void) { return g_launches; }
 
 extern "C" int bmg_profile_start(int kernel, int n) {
   if (kernel < 1 || kernel > 7 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");

@@ -161,8 +161,12 @@ int cuda_fail(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return bmg::cuda_fail(e_, #call);         \
   } while (0)
 
+namespace bmg {
+extern long long g_launches;   // kernels launched by this library (host-side count)
+}
 #define BMG_CHECK_LAUNCH(what)                                       \
   do {                                                               \
+    ++bmg::g_launches;                                               \
     cudaError_t e_ = cudaGetLastError();                             \
     if (e_ != cudaSuccess) return bmg::cuda_fail(e_, what);          \
   } while (0)

@@ -133,6 +133,7 @@ int coarse_setup(Level &L, int *d_flag, cudaStream_t st) {
     gj_pivot_kernel<<<1, 1024, 0, st>>>(Aug, N, k, fac, 1e-300, d_flag);
     gj_eliminate_kernel<<<dim3((2 * N + 255) / 256, N), 256, 0, st>>>(Aug, N, k, fac);
   }
+  g_launches += 2 * (long long)N - 1;
   BMG_CHECK_LAUNCH("gauss_jordan");
   BMG_CUDA(cudaMalloc(&L.cinv64, sizeof(double) * (size_t)N * N));
   BMG_CUDA(cudaMalloc(&L.cinv32, sizeof(float) * (size_t)N * N));
