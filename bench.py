@@ -157,6 +157,48 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------------------
+def run_micro(args):
+    """One fine-level kernel family on an n x n grid with a lognormal permeability (the
+    mixed-precision workload's coefficients), timed with the library's CUDA-event timer."""
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+    n = args.n
+    torch.cuda.set_device(0)
+    kL, kU = synthetic.lognormal_k(n, 2.0, 0)
+    K = torch.from_numpy(bmg.pack_k(n, kL, kU)).cuda()
+    s = bmg.assemble(n, 1e4, 1.0, K, 0.0, 1.0, 1.0, INV_M)
+    x = torch.from_numpy(bmg.pack(n, synthetic.uniform_field(n, 1))).cuda()
+    y = torch.empty_like(x)
+    h = None
+    if args.micro != "apply":
+        h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision=args.precision)
+    fam = {"apply": "apply", "vanka": "vanka", "vcycle": "vanka"}[args.micro]
+    def run():
+        if args.micro == "apply":
+            s.apply(x, y)
+        else:
+            h.vcycle(x, y)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    bmg.profile_start(fam, n)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.reps):
+        run()
+    ev1.record()
+    torch.cuda.synchronize()
+    prof = bmg.profile_stop()
+    avg = prof["ms"] / max(prof["launches"], 1)
+    cells = prof["cells"] / max(prof["launches"], 1)
+    print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision,
+                      "call_ms": ev0.elapsed_time(ev1) / args.reps, "kernel": fam,
+                      "kernel_avg_ms": avg, "launches": prof["launches"],
+                      "gflops_fp64": FLOPS_PER_CELL[fam] * cells / (avg * 1e-3) / 1e9,
+                      "gbs_algorithmic": BYTES_PER_CELL_F64[fam] * cells / (avg * 1e-3) / 1e9}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +209,10 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--micro", choices=["apply", "vanka", "vcycle"], default=None,
+                    help="time one kernel family (fine level) on --n instead of the workload")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -174,6 +220,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.micro:
+        run_micro(args)
         return
 
     import numpy as np
