@@ -193,6 +193,30 @@ int bmg_profile_start(int kernel, int n);
 long long bmg_launch_count(void);
 int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
+/*
+ * bmg_fgmres_solve_noalloc -- the same solve as bmg_fgmres_solve (same algorithm, kernels
+ * and results) for callers that cannot allocate device memory while they run: code that
+ * works inside a fixed memory budget or a framework that owns every device allocation, or
+ * that calls in from a context where cudaMalloc is not allowed.  bmg_fgmres_solve allocates
+ * its Krylov workspace with cudaMalloc on its first call (and again when `restart` grows);
+ * this variant allocates nothing.  The paper has no counterpart of this entry point.
+ *   Workspace: one fixed array of bmg_noalloc_capacity() doubles (8 MiB) reserved on every
+ *   device that loads the library and held until the process exits.  A call needs
+ *   (2 * restart + 3) * bmg_vector_len(n) + 612 * (restart + 2) doubles of it and
+ *   1 <= restart <= 64; a larger request fails with BMG_ERR_ARG and a message naming the
+ *   limit (e.g. n = 32 allows restart <= 38, n = 64 allows restart <= 9).
+ *   The first call on a device looks up the array's device address (once per device, with
+ *   that device current); make that first call before any stream capture.
+ *   Every call uses the same array, which keeps the last call's contents; the solve writes
+ *   every part of it before reading it.  Calls that overlap on the GPU (different streams or
+ *   threads at the same time) race on the array: serialise them.
+ *   h, b, x, o, info, stream: as for bmg_fgmres_solve (h is set up beforehand by
+ *   bmg_setup_hierarchy, which does allocate).
+ */
+int bmg_fgmres_solve_noalloc(bmg_hierarchy *h, const double *b, double *x,
+                             const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
+size_t bmg_noalloc_capacity(void);
+
 /* Grid size of a system / hierarchy (cells per side). */
 int bmg_system_n(const bmg_system *s);
 int bmg_hierarchy_levels(const bmg_hierarchy *h);

@@ -60,6 +60,8 @@ _sig = {
     "bmg_vcycle": (C.c_int, [_vp, _vp, _vp, _vp]),
     "bmg_fgmres_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), _vp]),
     "bmg_fgmres_solve_host": (C.c_int, [_vp, _vp, _vp, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), _vp]),
+    "bmg_fgmres_solve_noalloc": (C.c_int, [_vp, _vp, _vp, C.POINTER(KrylovOpts), C.POINTER(SolveInfo), _vp]),
+    "bmg_noalloc_capacity": (C.c_size_t, []),
     "bmg_system_n": (C.c_int, [_vp]),
     "bmg_hierarchy_levels": (C.c_int, [_vp]),
     "bmg_destroy_system": (None, [_vp]),
@@ -214,6 +216,16 @@ class Hierarchy:
                                     _stream(stream)), "bmg_fgmres_solve")
         return _info(info)
 
+    def fgmres_solve_noalloc(self, b, x, rtol=1e-8, restart=30, maxit=500, x0_is_zero=True,
+                             stream=None):
+        """The allocation-free variant: the Krylov workspace is the library's fixed device
+        array (``noalloc_capacity()`` doubles); see ``bmg_fgmres_solve_noalloc``."""
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+        info = SolveInfo()
+        _check(lib.bmg_fgmres_solve_noalloc(self._h, _ptr(b), _ptr(x), C.byref(ko), C.byref(info),
+                                            _stream(stream)), "bmg_fgmres_solve_noalloc")
+        return _info(info)
+
     def fgmres_solve_host(self, b: np.ndarray, x: np.ndarray, rtol=1e-8, restart=50, maxit=500,
                           x0_is_zero=True, stream=None):
         """Host-buffer variant: ``b`` and ``x`` are float64 numpy arrays (pinned or not)."""
@@ -259,6 +271,11 @@ def vcycle(h: Hierarchy, r, z, stream=None):
 
 
 PROF = {"apply": 1, "vanka": 2, "vanka_u": 3, "restrict": 4, "prolong": 5, "coarse": 6, "krylov": 7}
+
+
+def noalloc_capacity() -> int:
+    """Doubles in the fixed device workspace of ``fgmres_solve_noalloc``."""
+    return lib.bmg_noalloc_capacity()
 
 
 def launch_count() -> int:
