@@ -404,10 +404,13 @@ extern "C" void bmg_destroy_hierarchy(bmg_hierarchy *h) {
 }
 
 // ---- V-cycle ---------------------------------------------------------------------------
+// One relaxation x <- x + omega M^{-1} r; assign: x is zero on entry (first pre-smoothing
+// step from the zero initial guess), so the kernel writes x instead of updating it.
 template <typename T>
-static int smooth(bmg_hierarchy *h, const Level &L, const T *r, T *x, cudaStream_t st) {
-  if (h->opts.smoother == BMG_VANKA) return launch_vanka_sweep<T>(L, r, x, (T)h->opts.omega, st);
-  return launch_bsr_sweep<T>(L, r, x, (T)h->opts.omega, st);
+static int smooth(bmg_hierarchy *h, const Level &L, const T *r, T *x, cudaStream_t st,
+                  bool assign = false) {
+  if (h->opts.smoother == BMG_VANKA) return launch_vanka_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);
+  return launch_bsr_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);
 }
 
 template <typename T>
@@ -417,10 +420,10 @@ static int vcycle_level(bmg_hierarchy *h, size_t l, const T *rhs, T *z, cudaStre
   int rc;
   const size_t vl = vec_len_of(L.n);
   T *t = (T *)L.t;
-  if ((rc = launch_fill<T>(z, T(0), vl, st))) return rc;
+  if (h->opts.nu1 == 0 && (rc = launch_fill<T>(z, T(0), vl, st))) return rc;
   for (int s = 0; s < h->opts.nu1; ++s) {
     if (s == 0) {
-      rc = smooth<T>(h, L, rhs, z, st);          // zero initial guess: residual = rhs
+      rc = smooth<T>(h, L, rhs, z, st, true);    // zero initial guess: residual = rhs
     } else {
       if ((rc = launch_apply<T>(L, z, rhs, t, true, 1, 0, st))) return rc;
       rc = smooth<T>(h, L, t, z, st);
@@ -544,11 +547,10 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if ((rc = vcycle_any(h, vj, zj, st))) return rc;
       if ((rc = launch_apply<double>(s->fine, zj, nullptr, h->w, false, 1, 0, st))) return rc;
       double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
+      // CGS2: h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with ||w||^2
       if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d1, st))) return rc;
-      if ((rc = launch_update(h->w, h->V, ldv, j + 1, d1, vl, st))) return rc;
-      if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d2, st))) return rc;
-      if ((rc = launch_update(h->w, h->V, ldv, j + 1, d2, vl, st))) return rc;
-      if ((rc = launch_dots(nullptr, vl, 0, h->w, vl, h->partial, kDotBlocks, d3, st))) return rc;
+      if ((rc = launch_update_dots(h->w, h->V, ldv, j + 1, d1, vl, 1, h->partial, kDotBlocks, d2, st))) return rc;
+      if ((rc = launch_update_dots(h->w, h->V, ldv, j + 1, d2, vl, 0, h->partial, kDotBlocks, d3, st))) return rc;
       BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
       BMG_CUDA(cudaStreamSynchronize(st));
       const double hn = std::sqrt(hr[2 * (m + 2)]);

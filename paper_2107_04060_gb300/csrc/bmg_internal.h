@@ -189,7 +189,7 @@ int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, in
 int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
                        double p_shift_area, int psize, int *d_flag, cudaStream_t st);
 template <typename T>
-int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st);
+int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign);
 template <typename T>
 int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, cudaStream_t st);
 template <typename T>
@@ -202,7 +202,7 @@ template <typename T>
 int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st);
 int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st);
 template <typename T>
-int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st);
+int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign);
 // vector kernels
 template <typename T>
 int launch_fill(T *x, T v, size_t n, cudaStream_t st);
@@ -212,6 +212,8 @@ int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n,
                 double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_update(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                   cudaStream_t st);
+int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                       int dots, double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st);
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y,
                       size_t n, cudaStream_t st);

@@ -110,8 +110,6 @@ int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st
 // Displacement Vanka (8-DoF patches) applied to the u part of `r` plus the Jacobi step on
 // the w part.  mode 0: z_y = F^{-1} r_y written into `z` (u, w blocks);
 // mode 1: x_y += omega F^{-1} r_y and x_p += omega dp (dp from the p blocks of `d`).
-constexpr int kQX = 32, kQY = 8;
-
 template <typename T>
 struct VankaUArgs {
   Grid g;
@@ -125,22 +123,28 @@ struct VankaUArgs {
   const T *dinv;
   T omega;
   int mode;
+  int assign;    // mode 1 only: x was zero, write instead of add
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kQX *kQY) vanka_u_kernel(const __grid_constant__ VankaUArgs<T> a) {
-  __shared__ T sx[kQX * kQY][8];
+// kQX x kQY patches per CTA, NT threads; outputs (kQX - 1) x (kQY - 1).  Same three phases
+// as the 20-DoF sweep: residual gather, (patch, row) solve tasks, weighted gather.
+template <typename T, int kQX, int kQY, int NT>
+__global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ VankaUArgs<T> a) {
+  constexpr int NP = kQX * kQY, LD = 9;
+  __shared__ T sr[NP * LD];
+  __shared__ T sx[NP * LD];
+  __shared__ int ss[NP];
   const int n = a.g.n, P = a.g.pitch;
   const size_t blk = a.g.blk;
   const int i0 = blockIdx.x * (kQX - 1), j0 = blockIdx.y * (kQY - 1);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kQX + tx;
-  {
-    const int pi = i0 + tx, pj = j0 + ty;
+  const int tid = threadIdx.x;
+  for (int p = tid; p < NP; p += NT) {
+    const int pi = i0 + p % kQX, pj = j0 + p / kQX;
+    T *rl = sr + p * LD;
     if (pi <= n && pj <= n) {
       const T *r = a.r;
       const size_t o = (size_t)pj * P + pi;
       const bool li = pi >= 1, lj = pj >= 1;
-      T rl[8];
       rl[0] = r[UX * blk + o];
       rl[1] = r[UY * blk + o];
       rl[2] = r[BH * blk + o];
@@ -149,46 +153,66 @@ __global__ void __launch_bounds__(kQX *kQY) vanka_u_kernel(const __grid_constant
       rl[5] = lj ? r[BV * blk + o - P] : T(0);
       rl[6] = li ? r[BD * blk + o - 1] : T(0);
       rl[7] = lj ? r[BD * blk + o - P] : T(0);
-      const int s = a.slot[(size_t)pj * (n + 1) + pi];
-      const T *inv = a.inv + s;
-      const size_t ld = (size_t)a.nslots;
+      ss[p] = a.slot[(size_t)pj * (n + 1) + pi];
+    } else {
 #pragma unroll
-      for (int row = 0; row < 8; ++row) {
-        T acc = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc = fma(inv[(size_t)(row * 8 + c) * ld], rl[c], acc);
-        sx[tid][row] = acc;
-      }
+      for (int c = 0; c < 8; ++c) rl[c] = T(0);
+      ss[p] = 0;
     }
   }
   __syncthreads();
-  if (tx >= kQX - 1 || ty >= kQY - 1) return;
-  const int i = i0 + tx, j = j0 + ty;
-  if (i > n || j > n) return;
-  auto X = [&](int pi, int pj, int k) -> T { return sx[(pj - j0) * kQX + (pi - i0)][k]; };
-  bool m[NBLK];
-  dof_masks(i, j, n, m);
-  const size_t o = (size_t)j * P + i;
-  const T h = T(0.5);
-  T v[8];
-  v[UX] = m[UX] ? X(i, j, 0) : T(0);
-  v[UY] = m[UY] ? X(i, j, 1) : T(0);
-  v[BH] = m[BH] ? h * (X(i, j, 2) + X(i + 1, j, 4)) : T(0);
-  v[BV] = m[BV] ? h * (X(i, j, 3) + X(i, j + 1, 5)) : T(0);
-  v[BD] = m[BD] ? h * (X(i, j + 1, 7) + X(i + 1, j, 6)) : T(0);
-  v[WH] = m[WH] ? a.dinv[0 * blk + o] * a.r[WH * blk + o] : T(0);
-  v[WV] = m[WV] ? a.dinv[1 * blk + o] * a.r[WV * blk + o] : T(0);
-  v[WD] = m[WD] ? a.dinv[2 * blk + o] * a.r[WD * blk + o] : T(0);
-  if (a.mode == 0) {
+  const size_t ld = (size_t)a.nslots;
+  for (int t = tid; t < NP * 8; t += NT) {
+    const int row = t / NP, p = t % NP;
+    const T *inv = a.inv + ss[p] + (size_t)(row * 8) * ld;
+    const T *rl = sr + p * LD;
+    T acc = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a.z[k * blk + o] = v[k];
-  } else {
-    T *x = a.x;
+    for (int c = 0; c < 8; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
+    sx[p * LD + row] = acc;
+  }
+  __syncthreads();
+  for (int q = tid; q < (kQX - 1) * (kQY - 1); q += NT) {
+    const int i = i0 + q % (kQX - 1), j = j0 + q / (kQX - 1);
+    if (j > n) continue;
+    if (i > n) {                  // padding columns: written only when assigning
+      if ((a.mode == 1 && a.assign) && i < P) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (m[k]) x[k * blk + o] += a.omega * v[k];
-    if (m[PL]) x[PL * blk + o] += a.omega * a.d[PL * blk + o];
-    if (m[PU]) x[PU * blk + o] += a.omega * a.d[PU * blk + o];
+        for (int k = 0; k < NBLK; ++k) a.x[k * blk + (size_t)j * P + i] = T(0);
+      }
+      continue;
+    }
+    auto X = [&](int pi, int pj, int k) -> T { return sx[((pj - j0) * kQX + (pi - i0)) * LD + k]; };
+    bool m[NBLK];
+    dof_masks(i, j, n, m);
+    const size_t o = (size_t)j * P + i;
+    const T h = T(0.5);
+    T v[8];
+    v[UX] = m[UX] ? X(i, j, 0) : T(0);
+    v[UY] = m[UY] ? X(i, j, 1) : T(0);
+    v[BH] = m[BH] ? h * (X(i, j, 2) + X(i + 1, j, 4)) : T(0);
+    v[BV] = m[BV] ? h * (X(i, j, 3) + X(i, j + 1, 5)) : T(0);
+    v[BD] = m[BD] ? h * (X(i, j + 1, 7) + X(i + 1, j, 6)) : T(0);
+    v[WH] = m[WH] ? a.dinv[0 * blk + o] * a.r[WH * blk + o] : T(0);
+    v[WV] = m[WV] ? a.dinv[1 * blk + o] * a.r[WV * blk + o] : T(0);
+    v[WD] = m[WD] ? a.dinv[2 * blk + o] * a.r[WD * blk + o] : T(0);
+    if (a.mode == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a.z[k * blk + o] = v[k];
+    } else if (a.assign) {
+      T *x = a.x;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k * blk + o] = m[k] ? a.omega * v[k] : T(0);
+      x[PL * blk + o] = m[PL] ? a.omega * a.d[PL * blk + o] : T(0);
+      x[PU * blk + o] = m[PU] ? a.omega * a.d[PU * blk + o] : T(0);
+    } else {
+      T *x = a.x;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (m[k]) x[k * blk + o] += a.omega * v[k];
+      if (m[PL]) x[PL * blk + o] += a.omega * a.d[PL * blk + o];
+      if (m[PU]) x[PU * blk + o] += a.omega * a.d[PU * blk + o];
+    }
   }
 }
 
@@ -241,9 +265,15 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
   }
 }
 
+template <typename T, int QX, int QY, int NT>
+static void launch_vanka_u_tile(const VankaUArgs<T> &a, const Level &L, cudaStream_t st) {
+  dim3 grid((L.g.pitch + QX - 2) / (QX - 1), (L.n + 1 + QY - 2) / (QY - 1));
+  vanka_u_kernel<T, QX, QY, NT><<<grid, NT, 0, st>>>(a);
+}
+
 template <typename T>
 static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T omega, int mode,
-                          cudaStream_t st) {
+                          bool assign, cudaStream_t st) {
   const bool f64 = sizeof(T) == 8;
   VankaUArgs<T> a;
   a.g = L.g;
@@ -257,11 +287,18 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
   a.dinv = (const T *)(f64 ? (const void *)L.dinv64 : (const void *)L.dinv32);
   a.omega = omega;
   a.mode = mode;
-  dim3 block(kQX, kQY);
-  dim3 grid((L.n + 1 + kQX - 2) / (kQX - 1), (L.n + 1 + kQY - 2) / (kQY - 1));
-  { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
-  vanka_u_kernel<T><<<grid, block, 0, st>>>(a);
-    BMG_PROF_END(st, (double)L.n * L.n); }
+  a.assign = assign ? 1 : 0;
+  auto ctas = [&](int px, int py) {
+    return (long long)((L.g.pitch + px - 2) / (px - 1)) * ((L.n + 1 + py - 2) / (py - 1));
+  };
+  BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
+  const long long want = 2 * 152;
+  if (ctas(32, 8) >= want) launch_vanka_u_tile<T, 32, 8, 256>(a, L, st);
+  else if (ctas(16, 8) >= want) launch_vanka_u_tile<T, 16, 8, 256>(a, L, st);
+  else if (ctas(8, 8) >= want) launch_vanka_u_tile<T, 8, 8, 128>(a, L, st);
+  else if (ctas(8, 4) >= want) launch_vanka_u_tile<T, 8, 4, 128>(a, L, st);
+  else launch_vanka_u_tile<T, 4, 4, 64>(a, L, st);
+  BMG_PROF_END(st, (double)L.n * L.n);
   BMG_CHECK_LAUNCH("vanka_u_kernel");
   return BMG_OK;
 }
@@ -269,12 +306,12 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
 // One BSR relaxation x <- x + omega M^{-1} r.  Work vectors of the level: bz (z = F^{-1} r_y),
 // bd (dp in the p blocks; its u and w blocks stay zero), bry (r_y - B^T dp).
 template <typename T>
-int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st) {
+int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
   const bool f64 = sizeof(T) == 8;
   T *z = (T *)L.bz;
   T *d = (T *)L.bd;
   T *ry = (T *)L.bry;
-  int rc = launch_vanka_u<T>(L, r, z, nullptr, nullptr, omega, 0, st);
+  int rc = launch_vanka_u<T>(L, r, z, nullptr, nullptr, omega, 0, false, st);
   if (rc) return rc;
   DpArgs<T> a;
   a.g = L.g;
@@ -288,10 +325,10 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st)
   BMG_CHECK_LAUNCH("bsr_dp_kernel");
   // r_y - B^T dp: the residual of (0, 0, dp) against r (its p part is not used)
   if ((rc = launch_apply<T>(L, d, r, ry, true, 1, 0, st))) return rc;
-  return launch_vanka_u<T>(L, ry, nullptr, x, d, omega, 1, st);
+  return launch_vanka_u<T>(L, ry, nullptr, x, d, omega, 1, assign, st);
 }
 
-template int launch_bsr_sweep<double>(const Level &, const double *, double *, double, cudaStream_t);
-template int launch_bsr_sweep<float>(const Level &, const float *, float *, float, cudaStream_t);
+template int launch_bsr_sweep<double>(const Level &, const double *, double *, double, cudaStream_t, bool);
+template int launch_bsr_sweep<float>(const Level &, const float *, float *, float, cudaStream_t, bool);
 
 }  // namespace bmg

@@ -25,7 +25,6 @@ struct ApplyArgs {
   OpCoefs<T> c;
 };
 
-constexpr int kTX = 32, kTY = 8, kEX = kTX + 1, kEY = kTY + 1;
 
 // Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).
 template <typename T, int WM>
@@ -63,8 +62,12 @@ __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T 
   yl[12] = -c.alpha * gu - dww - c.pp * p;
 }
 
-template <typename T, int WM>
-__global__ void __launch_bounds__(kTX *kTY) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+// Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
+// tiles on the coarse levels so that their work spreads over many SMs).
+template <typename T, int WM, int kTX, int kTY, int NT>
+__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+  constexpr int kEX = kTX + 1, kEY = kTY + 1;
+  static_assert(NT >= kTX * kTY, "one thread per output position in phase 2");
   extern __shared__ unsigned char smem_raw[];
   T(*sy)[26] = reinterpret_cast<T(*)[26]>(smem_raw);
   const Grid g = a.g;
@@ -74,56 +77,49 @@ __global__ void __launch_bounds__(kTX *kTY) apply_kernel(const __grid_constant__
   const T *x = a.x + boff;
   T *y = a.y + boff;
   const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
-  const int tid = threadIdx.y * kTX + threadIdx.x;
+  const int tid = threadIdx.x;
 
-  for (int e = tid; e < kEX * kEY; e += kTX * kTY) {
-    const int ci = i0 - 1 + e % kEX, cj = j0 - 1 + e / kEX;
-    T *yl = sy[e];
+  // phase 1: one task per triangle of the tile plus its low-side halo (task = 2 * cell + o)
+  for (int e = tid; e < 2 * kEX * kEY; e += NT) {
+    const int cell = e >> 1, o = e & 1;
+    const int ci = i0 - 1 + cell % kEX, cj = j0 - 1 + cell / kEX;
+    T *yl = sy[cell] + 13 * o;
     if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
 #pragma unroll
-      for (int k = 0; k < 26; ++k) yl[k] = 0;
+      for (int k = 0; k < 13; ++k) yl[k] = 0;
       continue;
     }
     const size_t c00 = (size_t)cj * P + ci;          // (ci, cj)
-    const size_t c10 = c00 + 1, c01 = c00 + P, c11 = c00 + P + 1;
-    const bool f00 = vfree(ci, cj, n), f10 = vfree(ci + 1, cj, n);
-    const bool f01 = vfree(ci, cj + 1, n), f11 = vfree(ci + 1, cj + 1, n);
-    const T ux00 = f00 ? x[UX * blk + c00] : T(0), uy00 = f00 ? x[UY * blk + c00] : T(0);
-    const T ux10 = f10 ? x[UX * blk + c10] : T(0), uy10 = f10 ? x[UY * blk + c10] : T(0);
-    const T ux01 = f01 ? x[UX * blk + c01] : T(0), uy01 = f01 ? x[UY * blk + c01] : T(0);
-    const T ux11 = f11 ? x[UX * blk + c11] : T(0), uy11 = f11 ? x[UY * blk + c11] : T(0);
-    const T bd = x[BD * blk + c00], wd = x[WD * blk + c00];
-    const T bhL = (cj > 0) ? x[BH * blk + c00] : T(0), whL = x[WH * blk + c00];
-    const T bvL = (ci > 0) ? x[BV * blk + c00] : T(0), wvL = x[WV * blk + c00];
-    const T bhU = (cj + 1 < n) ? x[BH * blk + c01] : T(0), whU = x[WH * blk + c01];
-    const T bvU = (ci + 1 < n) ? x[BV * blk + c10] : T(0), wvU = x[WV * blk + c10];
-    const T pL = x[PL * blk + c00], pU = x[PU * blk + c00];
-    T kL = 0, kU = 0;
-    T wmL[6], wmU[6];
+    // L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj)
+    // U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1)
+    const int v0i = ci + o, v0j = cj + o;
+    const int v1i = o ? ci : ci + 1, v1j = o ? cj + 1 : cj;
+    const int v2i = o ? ci + 1 : ci, v2j = o ? cj : cj + 1;
+    const size_t a0 = (size_t)v0j * P + v0i, a1 = (size_t)v1j * P + v1i, a2 = (size_t)v2j * P + v2i;
+    const bool f0 = vfree(v0i, v0j, n), f1 = vfree(v1i, v1j, n), f2 = vfree(v2i, v2j, n);
+    const size_t ev = o ? c00 + 1 : c00;             // v(ci + o, cj)
+    const size_t eh = o ? c00 + P : c00;             // h(ci, cj + o)
+    const bool bvf = o ? (ci + 1 < n) : (ci > 0);
+    const bool bhf = o ? (cj + 1 < n) : (cj > 0);
+    const T u[9] = {f0 ? x[UX * blk + a0] : T(0), f1 ? x[UX * blk + a1] : T(0), f2 ? x[UX * blk + a2] : T(0),
+                    f0 ? x[UY * blk + a0] : T(0), f1 ? x[UY * blk + a1] : T(0), f2 ? x[UY * blk + a2] : T(0),
+                    x[BD * blk + c00], bvf ? x[BV * blk + ev] : T(0), bhf ? x[BH * blk + eh] : T(0)};
+    const T w[3] = {x[WD * blk + c00], x[WV * blk + ev], x[WH * blk + eh]};
+    const T p = x[(o ? PU : PL) * blk + c00];
+    T kin = 0;
+    T wm[6];
     if (WM == 0) {
-      kL = a.kinv[c00];
-      kU = a.kinv[blk + c00];
+      kin = a.kinv[(size_t)o * blk + c00];
     } else {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        wmL[k] = a.wm[(size_t)k * blk + c00];
-        wmU[k] = a.wm[(size_t)(6 + k) * blk + c00];
-      }
+      for (int k = 0; k < 6; ++k) wm[k] = a.wm[(size_t)(6 * o + k) * blk + c00];
     }
-    {  // L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj)
-      const T u[9] = {ux00, ux10, ux01, uy00, uy10, uy01, bd, bvL, bhL};
-      const T w[3] = {wd, wvL, whL};
-      tri_product<T, WM>(a.c, 0, u, w, pL, kL, wmL, yl);
-    }
-    {  // U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1)
-      const T u[9] = {ux11, ux01, ux10, uy11, uy01, uy10, bd, bvU, bhU};
-      const T w[3] = {wd, wvU, whU};
-      tri_product<T, WM>(a.c, 1, u, w, pU, kU, wmU, yl + 13);
-    }
+    tri_product<T, WM>(a.c, o, u, w, p, kin, wm, yl);
   }
   __syncthreads();
 
-  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (tid >= kTX * kTY) return;
+  const int i = i0 + tid % kTX, j = j0 + tid / kTX;
   if (j > n || i >= P) return;
   const size_t o = (size_t)j * P + i;
   if (i > n) {                                       // padding columns
@@ -158,6 +154,41 @@ __global__ void __launch_bounds__(kTX *kTY) apply_kernel(const __grid_constant__
   }
 }
 
+template <typename T, int WM, int TX, int TY, int NT>
+static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
+  dim3 block(NT);
+  dim3 grid((L.g.pitch + TX - 1) / TX, (L.n + 1 + TY - 1) / TY, batch);
+  const size_t smem = sizeof(T) * 26 * (TX + 1) * (TY + 1);
+  if (smem > 48 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr = true;
+    }
+  }
+  apply_kernel<T, WM, TX, TY, NT><<<grid, block, smem, st>>>(a);
+  return BMG_OK;
+}
+
+// CTAs a tile shape would launch on this level.
+static long long ctas_for(const Level &L, int tx, int ty, int batch) {
+  return (long long)((L.g.pitch + tx - 1) / tx) * ((L.n + 1 + ty - 1) / ty) * batch;
+}
+
+template <typename T, int WM>
+static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
+  // the largest tile that still gives every SM about two CTAs
+  const long long want = 2 * 152;
+  // small tiles get more threads than positions so that the triangle products (phase 1)
+  // of a tile are spread over more warps
+  if (ctas_for(L, 32, 8, batch) >= want) return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
+  if (ctas_for(L, 16, 8, batch) >= want) return launch_apply_tile<T, WM, 16, 8, 128>(a, L, batch, st);
+  if (ctas_for(L, 8, 8, batch) >= want) return launch_apply_tile<T, WM, 8, 8, 128>(a, L, batch, st);
+  if (ctas_for(L, 8, 4, batch) >= want) return launch_apply_tile<T, WM, 8, 4, 96>(a, L, batch, st);
+  return launch_apply_tile<T, WM, 4, 4, 64>(a, L, batch, st);
+}
+
 template <typename T>
 int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, int batch,
                  size_t bstride, cudaStream_t st) {
@@ -172,26 +203,10 @@ int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, in
   a.kinv = (const T *)(f64 ? (const void *)L.kinv64 : (const void *)L.kinv32);
   a.wm = (const T *)(f64 ? (const void *)L.wm64 : (const void *)L.wm32);
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
-  dim3 block(kTX, kTY);
-  dim3 grid((L.g.pitch + kTX - 1) / kTX, (L.n + 1 + kTY - 1) / kTY, batch);
-  const size_t smem = sizeof(T) * 26 * kEX * kEY;
   BMG_PROF_BEGIN(BMG_PROF_APPLY, L.n, st);
-  if (L.wm_full) {
-    static bool attr = false;
-    if (!attr) {
-      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr = true;
-    }
-    apply_kernel<T, 1><<<grid, block, smem, st>>>(a);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr = true;
-    }
-    apply_kernel<T, 0><<<grid, block, smem, st>>>(a);
-  }
+  int rc = L.wm_full ? launch_apply_wm<T, 1>(a, L, batch, st) : launch_apply_wm<T, 0>(a, L, batch, st);
   BMG_PROF_END(st, (double)L.n * L.n * batch);
+  if (rc) return rc;
   BMG_CHECK_LAUNCH("apply_kernel");
   return BMG_OK;
 }

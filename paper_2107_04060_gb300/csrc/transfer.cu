@@ -27,64 +27,61 @@ int upload_transfer_tables() {
   return BMG_OK;
 }
 
+// One thread per (coarse position, DoF type): blockIdx.z is the type.
 template <typename T>
 __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ct = blockIdx.z;
   const int nc = gc.n, nf = gf.n;
   if (I >= gc.pitch || J > nc) return;
   const size_t o = (size_t)J * gc.pitch + I;
-  if (I > nc) {
-#pragma unroll
-    for (int k = 0; k < NBLK; ++k) rc[k * gc.blk + o] = 0;
-    return;
-  }
-  bool m[NBLK];
-  dof_masks(I, J, nc, m);
-  for (int ct = 0; ct < NBLK; ++ct) {
-    T acc = 0;
+  T acc = 0;
+  if (I <= nc) {
+    bool m[NBLK];
+    dof_masks(I, J, nc, m);
     if (m[ct]) {
       const int ne = c_nres[ct];
       for (int e = 0; e < ne; ++e) {
         const StencilEntry se = c_res[ct][e];
         const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
         if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
-        acc += (T)se.coef * rf[se.type * gf.blk + (size_t)fj * gf.pitch + fi];
+        acc += (T)se.coef * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
       }
     }
-    rc[ct * gc.blk + o] = acc;
   }
+  rc[ct * gc.blk + o] = acc;
 }
 
+// One thread per (fine position, DoF type): blockIdx.z is the type.
 template <typename T>
 __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int t = blockIdx.z;
   const int nf = gf.n, nc = gc.n;
   if (i > nf || j > nf) return;
   bool m[NBLK];
   dof_masks(i, j, nf, m);
+  if (!m[t]) return;
   const int par = (i & 1) + 2 * (j & 1);
   const int I0 = i >> 1, J0 = j >> 1;
   const size_t o = (size_t)j * gf.pitch + i;
-  for (int t = 0; t < NBLK; ++t) {
-    if (!m[t]) continue;
-    T acc = 0;
-    const int ne = c_npro[t][par];
-    for (int e = 0; e < ne; ++e) {
-      const StencilEntry se = c_pro[t][par][e];
-      const int I = I0 + se.di, J = J0 + se.dj;
-      if (I < 0 || J < 0 || I > nc || J > nc) continue;
-      acc += (T)se.coef * xc[se.type * gc.blk + (size_t)J * gc.pitch + I];
-    }
-    xf[t * gf.blk + o] += acc;
+  T acc = 0;
+  const int ne = c_npro[t][par];
+  for (int e = 0; e < ne; ++e) {
+    const StencilEntry se = c_pro[t][par][e];
+    const int I = I0 + se.di, J = J0 + se.dj;
+    if (I < 0 || J < 0 || I > nc || J > nc) continue;
+    acc += (T)se.coef * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
   }
+  xf[t * gf.blk + o] += acc;
 }
 
 template <typename T>
 int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, cudaStream_t st) {
   dim3 block(32, 4);
-  dim3 grid((coarse.g.pitch + 31) / 32, (coarse.n + 1 + 3) / 4);
+  dim3 grid((coarse.g.pitch + 31) / 32, (coarse.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_RESTRICT, fine.n, st);
   restrict_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, rf, rc);
     BMG_PROF_END(st, (double)fine.n * fine.n); }
@@ -96,7 +93,7 @@ template <typename T>
 int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *xf,
                        cudaStream_t st) {
   dim3 block(32, 4);
-  dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4);
+  dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_PROLONG, fine.n, st);
   prolong_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, xc, xf);
     BMG_PROF_END(st, (double)fine.n * fine.n); }

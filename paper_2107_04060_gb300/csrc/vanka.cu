@@ -186,8 +186,12 @@ int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int n
 }
 
 // --------------------------------------------------------------------------------------
-constexpr int kPX = 32, kPY = 8;   // patches per CTA; outputs per CTA: 31 x 7
-
+// A CTA of NT threads holds kPX x kPY patches and updates the (kPX - 1) x (kPY - 1) positions
+// whose patches it holds.  Phase 1 gathers the patches' residuals into shared memory; phase
+// 2 splits the 20 x 20 local solves into (patch, row) tasks, so on small grids each thread
+// issues 20 * (rows per thread) FP64 FMAs instead of 400 (the FP64 pipe of a GB300 SM
+// retires about two FMAs per clock, so the per-warp instruction count sets the time);
+// phase 3 gathers the weighted corrections.  Deterministic, no atomics.
 template <typename T>
 struct VankaSweepArgs {
   Grid g;
@@ -197,29 +201,33 @@ struct VankaSweepArgs {
   const T *inv;
   int nslots;
   T omega;
+  int assign;   // 1: x <- omega M^{-1} r on the free DoFs (x was zero); 0: x += omega M^{-1} r
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kPX *kPY) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
-  __shared__ T sx[kPX * kPY][20];
+template <typename T, int kPX, int kPY, int NT>
+__global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+  constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
+  __shared__ T sr[NP * LD];
+  __shared__ T sx[NP * LD];
+  __shared__ int ss[NP];
   const int n = a.g.n, P = a.g.pitch;
   const size_t blk = a.g.blk;
   const int i0 = blockIdx.x * (kPX - 1), j0 = blockIdx.y * (kPY - 1);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
-  {
-    const int pi = i0 + tx, pj = j0 + ty;
+  const int tid = threadIdx.x;
+  // phase 1: residual gather, one patch per thread
+  for (int p = tid; p < NP; p += NT) {
+    const int pi = i0 + p % kPX, pj = j0 + p / kPX;
+    T *rl = sr + p * LD;
     if (pi <= n && pj <= n) {
       const T *r = a.r;
       const size_t o = (size_t)pj * P + pi;
-      T rl[20];
+      const bool li = pi >= 1, lj = pj >= 1;
       rl[0] = r[UX * blk + o];
       rl[1] = r[UY * blk + o];
-      // E0 = h(pi,pj), E1 = v(pi,pj) (slots beyond the grid hold zeros)
-      rl[2] = r[BH * blk + o];
+      rl[2] = r[BH * blk + o];                          // E0 = h(pi,pj)
       rl[8] = r[WH * blk + o];
-      rl[3] = r[BV * blk + o];
+      rl[3] = r[BV * blk + o];                          // E1 = v(pi,pj)
       rl[9] = r[WV * blk + o];
-      const bool li = pi >= 1, lj = pj >= 1;
       rl[4] = li ? r[BH * blk + o - 1] : T(0);          // E2 = h(pi-1,pj)
       rl[10] = li ? r[WH * blk + o - 1] : T(0);
       rl[5] = lj ? r[BV * blk + o - P] : T(0);          // E3 = v(pi,pj-1)
@@ -234,42 +242,79 @@ __global__ void __launch_bounds__(kPX *kPY) vanka_sweep_kernel(const __grid_cons
       rl[17] = li ? r[PU * blk + o - 1] : T(0);         // U(pi-1,pj)
       rl[18] = (li && lj) ? r[PU * blk + o - P - 1] : T(0);   // U(pi-1,pj-1)
       rl[19] = lj ? r[PU * blk + o - P] : T(0);         // U(pi,pj-1)
-      const int s = a.slot[(size_t)pj * (n + 1) + pi];
-      const T *inv = a.inv + s;
-      const size_t ld = (size_t)a.nslots;
+      ss[p] = a.slot[(size_t)pj * (n + 1) + pi];
+    } else {
 #pragma unroll
-      for (int row = 0; row < 20; ++row) {
-        T acc = 0;
-#pragma unroll
-        for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)(row * 20 + c) * ld], rl[c], acc);
-        sx[tid][row] = acc;
-      }
+      for (int c = 0; c < 20; ++c) rl[c] = T(0);
+      ss[p] = 0;
     }
   }
   __syncthreads();
-  if (tx >= kPX - 1 || ty >= kPY - 1) return;
-  const int i = i0 + tx, j = j0 + ty;
-  if (i > n || j > n) return;
-  auto X = [&](int pi, int pj, int k) -> T { return sx[(pj - j0) * kPX + (pi - i0)][k]; };
-  bool m[NBLK];
-  dof_masks(i, j, n, m);
-  T *x = a.x;
-  const size_t o = (size_t)j * P + i;
-  const T w = a.omega, half = T(0.5) * a.omega, third = a.omega / T(3);
-  if (m[UX]) x[UX * blk + o] += w * X(i, j, 0);
-  if (m[UY]) x[UY * blk + o] += w * X(i, j, 1);
-  if (m[BH]) x[BH * blk + o] += half * (X(i, j, 2) + X(i + 1, j, 4));
-  if (m[BV]) x[BV * blk + o] += half * (X(i, j, 3) + X(i, j + 1, 5));
-  if (m[BD]) x[BD * blk + o] += half * (X(i, j + 1, 7) + X(i + 1, j, 6));
-  if (m[WH]) x[WH * blk + o] += half * (X(i, j, 8) + X(i + 1, j, 10));
-  if (m[WV]) x[WV * blk + o] += half * (X(i, j, 9) + X(i, j + 1, 11));
-  if (m[WD]) x[WD * blk + o] += half * (X(i, j + 1, 13) + X(i + 1, j, 12));
-  if (m[PL]) x[PL * blk + o] += third * (X(i, j, 14) + X(i + 1, j, 15) + X(i, j + 1, 16));
-  if (m[PU]) x[PU * blk + o] += third * (X(i + 1, j + 1, 18) + X(i, j + 1, 19) + X(i + 1, j, 17));
+  // phase 2: xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads take
+  // consecutive patches of one row, so their inverse loads coalesce (or broadcast)
+  const size_t ld = (size_t)a.nslots;
+  for (int t = tid; t < NP * 20; t += NT) {
+    const int row = t / NP, p = t % NP;
+    const T *inv = a.inv + ss[p] + (size_t)(row * 20) * ld;
+    const T *rl = sr + p * LD;
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
+    sx[p * LD + row] = acc;
+  }
+  __syncthreads();
+  // phase 3: weighted gather of the corrections, one position per thread
+  for (int q = tid; q < (kPX - 1) * (kPY - 1); q += NT) {
+    const int i = i0 + q % (kPX - 1), j = j0 + q / (kPX - 1);
+    if (j > n) continue;
+    if (i > n) {                  // padding columns: written only when assigning
+      if (a.assign && i < P) {
+#pragma unroll
+        for (int k = 0; k < NBLK; ++k) a.x[k * blk + (size_t)j * P + i] = T(0);
+      }
+      continue;
+    }
+    auto X = [&](int pi, int pj, int k) -> T { return sx[((pj - j0) * kPX + (pi - i0)) * LD + k]; };
+    bool m[NBLK];
+    dof_masks(i, j, n, m);
+    T *x = a.x;
+    const size_t o = (size_t)j * P + i;
+    const T w = a.omega, half = T(0.5) * a.omega, third = a.omega / T(3);
+    T v[NBLK];
+    v[UX] = w * X(i, j, 0);
+    v[UY] = w * X(i, j, 1);
+    v[BH] = half * (X(i, j, 2) + X(i + 1, j, 4));
+    v[BV] = half * (X(i, j, 3) + X(i, j + 1, 5));
+    v[BD] = half * (X(i, j + 1, 7) + X(i + 1, j, 6));
+    v[WH] = half * (X(i, j, 8) + X(i + 1, j, 10));
+    v[WV] = half * (X(i, j, 9) + X(i, j + 1, 11));
+    v[WD] = half * (X(i, j + 1, 13) + X(i + 1, j, 12));
+    v[PL] = third * (X(i, j, 14) + X(i + 1, j, 15) + X(i, j + 1, 16));
+    v[PU] = third * (X(i + 1, j + 1, 18) + X(i, j + 1, 19) + X(i + 1, j, 17));
+    if (a.assign) {
+#pragma unroll
+      for (int k = 0; k < NBLK; ++k) x[k * blk + o] = m[k] ? v[k] : T(0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NBLK; ++k)
+        if (m[k]) x[k * blk + o] += v[k];
+    }
+  }
+}
+
+template <typename T, int PX, int PY, int NT>
+static void launch_vanka_tile(const VankaSweepArgs<T> &a, const Level &L, cudaStream_t st) {
+  static_assert(2 * PX * PY * 21 * sizeof(T) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
+  dim3 grid((L.g.pitch + PX - 2) / (PX - 1), (L.n + 1 + PY - 2) / (PY - 1));
+  vanka_sweep_kernel<T, PX, PY, NT><<<grid, NT, 0, st>>>(a);
+}
+
+static long long vanka_ctas(const Level &L, int px, int py) {
+  return (long long)((L.g.pitch + px - 2) / (px - 1)) * ((L.n + 1 + py - 2) / (py - 1));
 }
 
 template <typename T>
-int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st) {
+int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
   VankaSweepArgs<T> a;
   a.g = L.g;
   a.r = r;
@@ -278,16 +323,27 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   a.inv = (const T *)(sizeof(T) == 8 ? (const void *)L.pinv64 : (const void *)L.pinv32);
   a.nslots = L.nslots;
   a.omega = omega;
-  dim3 block(kPX, kPY);
-  dim3 grid((L.n + 1 + kPX - 2) / (kPX - 1), (L.n + 1 + kPY - 2) / (kPY - 1));
-  { BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
-  vanka_sweep_kernel<T><<<grid, block, 0, st>>>(a);
-    BMG_PROF_END(st, (double)L.n * L.n); }
+  a.assign = assign ? 1 : 0;
+  BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
+  // the largest patch tile that still gives every SM about two CTAs; smaller tiles also
+  // spread each patch's rows over more threads
+  // (two 21-wide shared arrays per patch: 32 x 8 patches fit the 48 KB static limit in FP32 only)
+  const long long want = 2 * 152;
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (vanka_ctas(L, 32, 8) >= want) { launch_vanka_tile<T, 32, 8, 256>(a, L, st); done = true; }
+  }
+  if (done) {
+  } else if (vanka_ctas(L, 16, 8) >= want) launch_vanka_tile<T, 16, 8, 256>(a, L, st);
+  else if (vanka_ctas(L, 8, 8) >= want) launch_vanka_tile<T, 8, 8, 256>(a, L, st);
+  else if (vanka_ctas(L, 8, 4) >= want) launch_vanka_tile<T, 8, 4, 160>(a, L, st);
+  else launch_vanka_tile<T, 4, 4, 160>(a, L, st);
+  BMG_PROF_END(st, (double)L.n * L.n);
   BMG_CHECK_LAUNCH("vanka_sweep_kernel");
   return BMG_OK;
 }
 
-template int launch_vanka_sweep<double>(const Level &, const double *, double *, double, cudaStream_t);
-template int launch_vanka_sweep<float>(const Level &, const float *, float *, float, cudaStream_t);
+template int launch_vanka_sweep<double>(const Level &, const double *, double *, double, cudaStream_t, bool);
+template int launch_vanka_sweep<float>(const Level &, const float *, float *, float, cudaStream_t, bool);
 
 }  // namespace bmg
