@@ -105,6 +105,14 @@ int bmg_assemble(int n, double lambda, double mu, const double *K, double K_cons
                  double tau, double alpha, double inv_M, void *stream, bmg_system **out);
 
 /*
+ * bmg_assemble_logk -- as bmg_assemble with the permeability given as its logarithm:
+ * logK is a device pointer to FP32 theta_T = log K_T per triangle in the layout of K
+ * (K^{-1} = exp(-theta) is formed on the device).  Used by the adjoint gradient below.
+ */
+int bmg_assemble_logk(int n, double lambda, double mu, const float *logK, double tau,
+                      double alpha, double inv_M, void *stream, bmg_system **out);
+
+/*
  * bmg_apply -- y = A x (FP64, matrix-free).  bmg_residual -- r = b - A x.
  * x, y, b, r: device vectors of bmg_vector_len(n) doubles; y/r may not alias x.
  */
@@ -172,6 +180,22 @@ int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
 /* Same with HOST vectors: copies b in, solves, copies x out (all on `stream`). */
 int bmg_fgmres_solve_host(bmg_hierarchy *h, const double *b_host, double *x_host,
                           const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
+
+/*
+ * bmg_adjoint_gradient -- parameter gradients of a loss L on the solution of A x = b, given
+ * x and the adjoint solution xi of A xi = dL/dx (A is symmetric, so xi comes from the same
+ * bmg_fgmres_solve with right-hand side dL/dx).  dL/dq = -xi^T (dA/dq) x with the element
+ * matrices of Sec. 2.3:
+ *   dtheta[T] = dL/dtheta_T = K_T^{-1} xi_w,T^T (tau M_T) w_T   (theta_T = log K_T, M_T the
+ *               unit-permeability RT0 mass), written per triangle in the layout of K (FP64,
+ *               unused slots 0);
+ *   dlame[0]  = dL/dlambda = -sum_T (g_T . xi_u,T)(g_T . u_T) / |T|;
+ *   dlame[1]  = dL/dmu     = -sum_T xi_u,T^T 2 A_eps,T u_T.
+ * All pointers are device pointers; the Lame sums are reduced in a fixed order.  The paper
+ * has no adjoint; this entry point serves the differentiable solve of the Python binding.
+ */
+int bmg_adjoint_gradient(const bmg_system *s, const double *x, const double *xi,
+                         double *dtheta, double *dlame, void *stream);
 
 /*
  * Kernel timing (tracing).  bmg_profile_start(kernel, n) makes every later launch of the

@@ -54,6 +54,9 @@ _sig = {
     "bmg_free_dofs": (C.c_size_t, [C.c_int]),
     "bmg_assemble": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
                                C.c_double, C.c_double, _vp, C.POINTER(_vp)]),
+    "bmg_assemble_logk": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
+                                    C.c_double, _vp, C.POINTER(_vp)]),
+    "bmg_adjoint_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bmg_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "bmg_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "bmg_setup_hierarchy": (C.c_int, [_vp, C.POINTER(MgOpts), _vp, C.POINTER(_vp)]),
@@ -169,6 +172,12 @@ class System:
     def residual(self, b, x, r, stream=None):
         _check(lib.bmg_residual(self._h, _ptr(b), _ptr(x), _ptr(r), _stream(stream)), "bmg_residual")
 
+    def adjoint_gradient(self, x, xi, dtheta, dlame, stream=None):
+        """``bmg_adjoint_gradient``: dtheta (2 blocks, layout of K) and dlame = (dL/dlambda,
+        dL/dmu), float64 CUDA tensors written by the library."""
+        _check(lib.bmg_adjoint_gradient(self._h, _ptr(x), _ptr(xi), _ptr(dtheta), _ptr(dlame),
+                                        _stream(stream)), "bmg_adjoint_gradient")
+
     def close(self):
         if self._h:
             lib.bmg_destroy_system(self._h)
@@ -191,6 +200,18 @@ def assemble(n: int, lam: float, mu: float, K=None, K_const: float = 1.0, tau: f
            "bmg_assemble")
     return System(h, n, dict(lam=lam, mu=mu, K_const=K_const, tau=tau, alpha=alpha, inv_M=inv_M,
                              K_field=K is not None))
+
+
+def assemble_logk(n: int, lam: float, mu: float, logK, tau: float = 1.0, alpha: float = 1.0,
+                  inv_M: float = 0.0, stream=None) -> System:
+    """``bmg_assemble_logk``: logK is a float32 CUDA tensor laid out as ``pack_k`` produces."""
+    import torch
+    if logK.dtype != torch.float32:
+        raise BmgError("assemble_logk: float32 log-permeability required")
+    h = _vp()
+    _check(lib.bmg_assemble_logk(n, lam, mu, _ptr(logK), tau, alpha, inv_M, _stream(stream), C.byref(h)),
+           "bmg_assemble_logk")
+    return System(h, n, dict(lam=lam, mu=mu, tau=tau, alpha=alpha, inv_M=inv_M, K_field=True))
 
 
 class Hierarchy:

@@ -46,6 +46,25 @@ __global__ void kinv_from_k_kernel(Grid g, const double *K, double *kinv64, floa
   }
 }
 
+// K^{-1} = exp(-theta) from a per-triangle log-permeability (FP32, same layout as K).
+__global__ void kinv_from_logk_kernel(Grid g, const float *theta, double *kinv64, float *kinv32,
+                                      int *flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.pitch || j > g.n) return;
+  for (int o = 0; o < 2; ++o) {
+    const size_t idx = (size_t)o * g.blk + (size_t)j * g.pitch + i;
+    double v = 0.0;
+    if (i < g.n && j < g.n) {
+      const double t = (double)theta[idx];
+      v = exp(-t);
+      if (!isfinite(t) || !(v > 0.0) || !isfinite(v)) atomicOr(flag, 4);
+    }
+    kinv64[idx] = v;
+    kinv32[idx] = (float)v;
+  }
+}
+
 static int alloc_coefs(Level &L, bool full) {
   const size_t blk = L.g.blk;
   if (!full) {
@@ -157,9 +176,9 @@ extern "C" const char *bmg_status_string(int code) {
 extern "C" const char *bmg_last_error(void) { return g_last_error.c_str(); }
 
 // ---- system ----------------------------------------------------------------------------
-extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, double K_const,
-                            double tau, double alpha, double inv_M, void *stream,
-                            bmg_system **out) {
+static int assemble_impl(int n, double lambda, double mu, const double *K, const float *logK,
+                         double K_const, double tau, double alpha, double inv_M, void *stream,
+                         bmg_system **out) {
   if (!out) return arg_error("bmg_assemble: out is NULL");
   *out = nullptr;
   if (n < 1 || n > 16384) return arg_error("bmg_assemble: n out of range [1, 16384]");
@@ -168,7 +187,7 @@ extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, do
       !(std::isfinite(inv_M) && inv_M >= 0.0))
     return arg_error("bmg_assemble: physical parameters must be finite with lambda > 0, "
                      "mu >= 0, tau > 0, inv_M >= 0");
-  if (!K && !(std::isfinite(K_const) && K_const > 0.0))
+  if (!K && !logK && !(std::isfinite(K_const) && K_const > 0.0))
     return arg_error("bmg_assemble: K_const must be finite and > 0 when K is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   int rc = upload_transfer_tables();
@@ -176,14 +195,16 @@ extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, do
   bmg_system *s = new bmg_system();
   s->n = n;
   s->prm = PhysParams{lambda, mu, tau, alpha, inv_M};
-  s->uniform = (K == nullptr);
+  s->uniform = (K == nullptr && logK == nullptr);
   s->K_const = K_const;
   Level &L = s->fine;
   L.n = n;
   L.g = grid_of(n);
   L.uniform = s->uniform;
   rc = alloc_coefs(L, false);
-  if (rc) { free_level(L); delete s; return rc; }
+  if (!rc && cudaMalloc(&s->adj_partial, sizeof(double) * 2 * kAdjBlocks) != cudaSuccess)
+    rc = cuda_fail(cudaErrorMemoryAllocation, "bmg_assemble");
+  if (rc) { free_level(L); cudaFree(s->adj_partial); delete s; return rc; }
   make_coefs(s->prm, n, &L.c64, &L.c32);
   if (s->uniform) {
     if ((rc = launch_fill<double>(L.kinv64, 1.0 / K_const, 2 * L.g.blk, st)) ||
@@ -196,15 +217,17 @@ extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, do
     if (e != cudaSuccess) { free_level(L); delete s; return cuda_fail(e, "cudaMalloc(flag)"); }
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     dim3 b(32, 8), gr((L.g.pitch + 31) / 32, (n + 1 + 7) / 8);
-    kinv_from_k_kernel<<<gr, b, 0, st>>>(L.g, K, L.kinv64, L.kinv32, flag);
+    if (K) kinv_from_k_kernel<<<gr, b, 0, st>>>(L.g, K, L.kinv64, L.kinv32, flag);
+    else kinv_from_logk_kernel<<<gr, b, 0, st>>>(L.g, logK, L.kinv64, L.kinv32, flag);
+    ++g_launches;
     int hflag = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(flag);
-    if (e != cudaSuccess) { free_level(L); delete s; return cuda_fail(e, "kinv_from_k"); }
+    if (e != cudaSuccess) { free_level(L); cudaFree(s->adj_partial); delete s; return cuda_fail(e, "kinv_from_k"); }
     if (hflag) {
-      free_level(L); delete s;
+      free_level(L); cudaFree(s->adj_partial); delete s;
       set_error("bmg_assemble: permeability must be finite and > 0 on every triangle");
       return BMG_ERR_NONFINITE;
     }
@@ -213,11 +236,24 @@ extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, do
   return BMG_OK;
 }
 
+extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, double K_const,
+                            double tau, double alpha, double inv_M, void *stream,
+                            bmg_system **out) {
+  return assemble_impl(n, lambda, mu, K, nullptr, K_const, tau, alpha, inv_M, stream, out);
+}
+
+extern "C" int bmg_assemble_logk(int n, double lambda, double mu, const float *logK, double tau,
+                                 double alpha, double inv_M, void *stream, bmg_system **out) {
+  if (!logK) return arg_error("bmg_assemble_logk: logK is NULL");
+  return assemble_impl(n, lambda, mu, nullptr, logK, 0.0, tau, alpha, inv_M, stream, out);
+}
+
 extern "C" int bmg_system_n(const bmg_system *s) { return s ? s->n : 0; }
 
 extern "C" void bmg_destroy_system(bmg_system *s) {
   if (!s) return;
   free_level(s->fine);
+  cudaFree(s->adj_partial);
   delete s;
 }
 

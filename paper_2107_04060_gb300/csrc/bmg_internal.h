@@ -127,12 +127,17 @@ struct Level {
 
 }  // namespace bmg
 
+namespace bmg {
+constexpr int kAdjBlocks = 152 * 8;   // CTAs of the adjoint-gradient reduction
+}
+
 struct bmg_system {
   int n;
   bmg::PhysParams prm;
   bool uniform;                // K given as a constant
   double K_const;
   bmg::Level fine;             // coefficients of the fine level (kinv64/kinv32, coefs)
+  double *adj_partial = nullptr;   // [2][kAdjBlocks] partial sums of the Lame gradients
 };
 
 struct bmg_hierarchy {
