@@ -165,15 +165,18 @@ def run_micro(args):
     import synthetic
     n = args.n
     torch.cuda.set_device(0)
-    kL, kU = synthetic.lognormal_k(n, 2.0, 0)
-    K = torch.from_numpy(bmg.pack_k(n, kL, kU)).cuda()
-    s = bmg.assemble(n, 1e4, 1.0, K, 0.0, 1.0, 1.0, INV_M)
+    if args.uniform_k:
+        s = bmg.assemble(n, 1e4, 1.0, None, 1.0, 1.0, 1.0, INV_M)
+    else:
+        kL, kU = synthetic.lognormal_k(n, 2.0, 0)
+        K = torch.from_numpy(bmg.pack_k(n, kL, kU)).cuda()
+        s = bmg.assemble(n, 1e4, 1.0, K, 0.0, 1.0, 1.0, INV_M)
     x = torch.from_numpy(bmg.pack(n, synthetic.uniform_field(n, 1))).cuda()
     y = torch.empty_like(x)
     h = None
     if args.micro != "apply":
         h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision=args.precision)
-    fam = {"apply": "apply", "vanka": "vanka", "vcycle": "vanka"}[args.micro]
+    fam = {"apply": "apply", "vanka": "vanka", "vcycle": args.family or "vanka"}[args.micro]
     def run():
         if args.micro == "apply":
             s.apply(x, y)
@@ -192,7 +195,9 @@ def run_micro(args):
     prof = bmg.profile_stop()
     avg = prof["ms"] / max(prof["launches"], 1)
     cells = prof["cells"] / max(prof["launches"], 1)
-    print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision,
+    bpc = BYTES_PER_CELL_F64[fam] * (0.5 if args.precision == "fp32" else 1.0)
+    print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision, "uniform_k": args.uniform_k,
+                      "gbs_algorithmic_this_precision": bpc * cells / (avg * 1e-3) / 1e9,
                       "call_ms": ev0.elapsed_time(ev1) / args.reps, "kernel": fam,
                       "kernel_avg_ms": avg, "launches": prof["launches"],
                       "gflops_fp64": FLOPS_PER_CELL[fam] * cells / (avg * 1e-3) / 1e9,
@@ -213,6 +218,9 @@ def main():
                     help="time one kernel family (fine level) on --n instead of the workload")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--uniform-k", action="store_true", help="--micro: constant K instead of lognormal")
+    ap.add_argument("--family", default=None, choices=["apply", "vanka"],
+                    help="--micro vcycle: kernel family to time (default vanka)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

@@ -79,9 +79,12 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ Apply
   const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
   const int tid = threadIdx.x;
 
-  // phase 1: one task per triangle of the tile plus its low-side halo (task = 2 * cell + o)
-  for (int e = tid; e < 2 * kEX * kEY; e += NT) {
-    const int cell = e >> 1, o = e & 1;
+  // phase 1: one task per triangle of the tile plus its low-side halo; all lower-left
+  // triangles come first so that a warp works on one orientation (no divergence between
+  // the two inlined element products)
+  constexpr int NE = kEX * kEY;
+  for (int e = tid; e < 2 * NE; e += NT) {
+    const int o = e >= NE ? 1 : 0, cell = e - o * NE;
     const int ci = i0 - 1 + cell % kEX, cj = j0 - 1 + cell / kEX;
     T *yl = sy[cell] + 13 * o;
     if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
@@ -114,7 +117,16 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ Apply
 #pragma unroll
       for (int k = 0; k < 6; ++k) wm[k] = a.wm[(size_t)(6 * o + k) * blk + c00];
     }
-    tri_product<T, WM>(a.c, o, u, w, p, kin, wm, yl);
+    // FP32: orientation as a compile-time constant, so the element coefficients become
+    // immediate constant-bank operands (the FP32 pipe would otherwise wait on indexed
+    // constant loads).  FP64: one shared body with the orientation as an index (fewer
+    // registers, more warps; the FP64 pipe is the limit either way).
+    if constexpr (sizeof(T) == 4) {
+      if (o == 0) tri_product<T, WM>(a.c, 0, u, w, p, kin, wm, yl);
+      else tri_product<T, WM>(a.c, 1, u, w, p, kin, wm, yl);
+    } else {
+      tri_product<T, WM>(a.c, o, u, w, p, kin, wm, yl);
+    }
   }
   __syncthreads();
 

@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
   __shared__ T sr[NP * LD];
   __shared__ T sx[NP * LD];
   __shared__ int ss[NP];
+  __shared__ int s_mixed;                          // some patch of the tile has its own inverse
+  if (threadIdx.x == 0) s_mixed = 0;
+  __syncthreads();
   const int n = a.g.n, P = a.g.pitch;
   const size_t blk = a.g.blk;
   const int i0 = blockIdx.x * (kPX - 1), j0 = blockIdx.y * (kPY - 1);
@@ -242,7 +245,9 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
       rl[17] = li ? r[PU * blk + o - 1] : T(0);         // U(pi-1,pj)
       rl[18] = (li && lj) ? r[PU * blk + o - P - 1] : T(0);   // U(pi-1,pj-1)
       rl[19] = lj ? r[PU * blk + o - P] : T(0);         // U(pi,pj-1)
-      ss[p] = a.slot[(size_t)pj * (n + 1) + pi];
+      const int sl = a.slot[(size_t)pj * (n + 1) + pi];
+      ss[p] = sl;
+      if (sl != 0) s_mixed = 1;
     } else {
 #pragma unroll
       for (int c = 0; c < 20; ++c) rl[c] = T(0);
@@ -250,17 +255,38 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
     }
   }
   __syncthreads();
-  // phase 2: xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads take
-  // consecutive patches of one row, so their inverse loads coalesce (or broadcast)
   const size_t ld = (size_t)a.nslots;
-  for (int t = tid; t < NP * 20; t += NT) {
-    const int row = t / NP, p = t % NP;
-    const T *inv = a.inv + ss[p] + (size_t)(row * 20) * ld;
-    const T *rl = sr + p * LD;
-    T acc = 0;
+  if (!s_mixed) {
+    // every patch of the tile uses the shared interior inverse (slot 0): thread
+    // (row = tid % 20, group = tid / 20) keeps its inverse row in registers and sweeps the
+    // group's patches, so the solve issues a few shared loads per patch instead of 400
+    // global loads.
+    constexpr int NG = NT / 20;
+    if (tid < NG * 20) {
+      const int row = tid % 20, grp = tid / 20;
+      T irow[20];
 #pragma unroll
-    for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
-    sx[p * LD + row] = acc;
+      for (int c = 0; c < 20; ++c) irow[c] = a.inv[(size_t)(row * 20 + c) * ld];
+      for (int p = grp; p < NP; p += NG) {
+        const T *rl = sr + p * LD;
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 20; ++c) acc = fma(irow[c], rl[c], acc);
+        sx[p * LD + row] = acc;
+      }
+    }
+  } else {
+    // phase 2 (general): xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads
+    // take consecutive patches of one row, so their inverse loads coalesce (or broadcast)
+    for (int t = tid; t < NP * 20; t += NT) {
+      const int row = t / NP, p = t % NP;
+      const T *inv = a.inv + ss[p] + (size_t)(row * 20) * ld;
+      const T *rl = sr + p * LD;
+      T acc = 0;
+#pragma unroll
+      for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
+      sx[p * LD + row] = acc;
+    }
   }
   __syncthreads();
   // phase 3: weighted gather of the corrections, one position per thread
