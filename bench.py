@@ -204,6 +204,103 @@ def run_micro(args):
                       "gbs_algorithmic": BYTES_PER_CELL_F64[fam] * cells / (avg * 1e-3) / 1e9}))
 
 
+def batched_instances(count: int, seed: int = 2026):
+    """The batched workload: `count` independent instances with n uniform in {32, 64, 128,
+    256}, lambda log-uniform in [1, 1e6], per-triangle lognormal K (sigma = 1), mu = tau =
+    alpha = 1/M = 1, right-hand side uniform in [-1, 1]; seeds fixed per instance."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        n = int(rng.choice([32, 64, 128, 256]))
+        lam = float(10.0 ** rng.uniform(0.0, 6.0))
+        out.append(dict(n=n, lam=lam, k_seed=1000 + q, b_seed=2000 + q,
+                        omega=0.8 if lam < 10.0 else 0.7))
+    return out
+
+
+def run_batched(args):
+    """Batched workload: every instance solved to 1e-8 by one graph launch of the batched
+    FGMRES, timed against the same instances solved one after the other with the
+    single-instance FGMRES (both with FP64 Vanka V(1,1) preconditioning)."""
+    import numpy as np
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    inst = batched_instances(args.batch_count)
+    t0 = time.perf_counter()
+    systems, hs, bs = [], [], []
+    for c in inst:
+        n = c["n"]
+        kL, kU = synthetic.lognormal_k(n, 1.0, c["k_seed"])
+        K = torch.from_numpy(bmg.pack_k(n, kL, kU)).to(dev)
+        s = bmg.assemble(n, c["lam"], 1.0, K, 0.0, 1.0, 1.0, INV_M)
+        systems.append(s)
+        hs.append(bmg.setup_hierarchy(s, "vanka", 1, 1, omega=c["omega"]))
+        bs.append(torch.from_numpy(bmg.pack(n, synthetic.rhs(n, c["b_seed"]))).to(dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    batch = bmg.Batch(hs, rtol=RTOL, restart=RESTART, maxit=MAXIT, autotune=not args.no_autotune)
+    create_s = time.perf_counter() - t1
+    xs = [torch.zeros_like(b) for b in bs]
+    ndof = sum(bmg.free_dofs(c["n"]) for c in inst)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        infos = batch.solve(bs, xs)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        l0 = bmg.launch_count()
+        ev0.record()
+        infos = batch.solve(bs, xs)
+        ev1.record()
+        torch.cuda.synchronize()
+        launches = bmg.launch_count() - l0
+        times.append(ev0.elapsed_time(ev1))
+    bad = [i for i in infos if i["status"] != "converged"]
+    if bad:
+        raise RuntimeError(f"batched solve: {len(bad)} instances did not converge")
+    # the same instances one after the other (single-instance FGMRES, host-driven)
+    seq_ms = None
+    seq_iters = []
+    if not args.no_sequential:
+        x = [torch.zeros_like(b) for b in bs]
+        for q in range(min(3, len(hs))):
+            hs[q].fgmres_solve(bs[q], x[q], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        ev0.record()
+        for q in range(len(hs)):
+            i = hs[q].fgmres_solve(bs[q], x[q], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            seq_iters.append(i["iters"])
+        ev1.record()
+        torch.cuda.synchronize()
+        seq_ms = ev0.elapsed_time(ev1)
+    ms = float(np.median(times))
+    iters = [i["iters"] for i in infos]
+    sizes = sorted({c["n"] for c in inst})
+    print(json.dumps({
+        "workload": f"batched {len(inst)} instances, n in {{32,64,128,256}}, lambda log-uniform [1,1e6], "
+                    "lognormal K sigma 1, FP64 Vanka V(1,1) FGMRES(50) to 1e-8",
+        "metric": "MDOF/s to 1e-8 rel. residual (batched)", "unit": "MDOF/s",
+        "value": ndof / (ms * 1e-3) / 1e6, "ms_per_solve": ms, "steps": args.steps,
+        "warmup": args.warmup, "free_dofs": ndof,
+        "sequential_ms": seq_ms,
+        "sequential_mdofs": (ndof / (seq_ms * 1e-3) / 1e6) if seq_ms else None,
+        "speedup_vs_sequential": (seq_ms / ms) if seq_ms else None,
+        "iters_min_median_max": [min(iters), float(np.median(iters)), max(iters)],
+        "iters_sum": sum(iters), "sequential_iters_sum": sum(seq_iters) if seq_iters else None,
+        "trips": batch.trips, "kernels_per_trip": batch.kernels_per_trip, "gpu_launches": launches,
+        "tiles": {str(n): [batch.tile("apply", n), batch.tile("vanka", n)] for n in sizes + [16]},
+        "setup_s": setup_s, "batch_create_s": create_s,
+        "autotune": not args.no_autotune}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +318,12 @@ def main():
     ap.add_argument("--uniform-k", action="store_true", help="--micro: constant K instead of lognormal")
     ap.add_argument("--family", default=None, choices=["apply", "vanka"],
                     help="--micro vcycle: kernel family to time (default vanka)")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched"],
+                    help="sweep: the 512^2 parameter sweep (default); batched: the batched "
+                         "workload (--batch-count instances), printed as its own line")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -231,6 +334,9 @@ def main():
         return
     if args.micro:
         run_micro(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
 
     import numpy as np

@@ -241,6 +241,46 @@ int bmg_fgmres_solve_noalloc(bmg_hierarchy *h, const double *b, double *x,
                              const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
 size_t bmg_noalloc_capacity(void);
 
+/*
+ * Batched solves -- many independent systems A_i x_i = b_i, each with its own grid size,
+ * coefficients and hierarchy, solved together by the FGMRES(m) + V-cycle iteration of Sec.
+ * 5.1 (the iteration of bmg_fgmres_solve, run for every instance).  The paper solves one
+ * system at a time; batching is this library's arrangement for many small problems.
+ *
+ * bmg_batch_create(hs, count, o, autotune, stream, out)
+ *   hs[count]: distinct hierarchies from bmg_setup_hierarchy, all with smoother BMG_VANKA,
+ *     precision BMG_FP64, nu1 >= 1 and the same nu1, nu2 and n_coarse (omega may differ).
+ *     The batch borrows their level data and work vectors: keep them alive, and do not use
+ *     them in other solves while a batch solve runs.  1 <= count <= 4096.
+ *   o: rtol, restart, maxit and x0_is_zero for every instance (as for bmg_fgmres_solve).
+ *   autotune != 0: time every candidate tile of the batched operator and Vanka kernels on
+ *     this batch (per level size) and keep the fastest; 0: the single-instance rule.
+ *   Allocates the Krylov workspace of every instance ((2m + 5) vectors of its size) and
+ *   records the solve as one CUDA graph: a prologue (copy-in, ||b||), a device-side while
+ *   loop whose body closes cycles and takes one Arnoldi step for every open instance, and
+ *   an epilogue (copy-out).  Returns BMG_ERR_ARG on an invalid batch (message names why).
+ * bmg_batch_solve(bt, b, x, infos, stream)
+ *   b[count], x[count]: device vectors (bmg_vector_len(n_i) doubles) of the instances, x not
+ *   aliasing b; x is the initial guess unless x0_is_zero.  One graph launch on `stream`,
+ *   then a wait for it.  infos[count] (nullable): per-instance results as for
+ *   bmg_fgmres_solve, solve_ms being the batch's wall time.  An instance whose b is not
+ *   finite is left at status BMG_DIVERGED and the call returns BMG_ERR_NONFINITE after the
+ *   others have been solved.
+ * bmg_batch_tile(bt, kernel, n): tile chosen for BMG_PROF_APPLY or BMG_PROF_VANKA at level
+ *   size n (index into the kernels' candidate list), -1 if none.
+ * bmg_batch_trips(bt): while-loop trips of the last solve (Arnoldi steps of the slowest
+ *   instance + 1).  bmg_batch_kernels_per_trip(bt): kernels in one trip.
+ */
+typedef struct bmg_batch bmg_batch;
+int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_krylov_opts *o, int autotune,
+                     void *stream, bmg_batch **out);
+int bmg_batch_solve(bmg_batch *bt, const double *const *b, double *const *x,
+                    bmg_solve_info *infos, void *stream);
+int bmg_batch_tile(const bmg_batch *bt, int kernel, int n);
+int bmg_batch_trips(const bmg_batch *bt);
+long long bmg_batch_kernels_per_trip(const bmg_batch *bt);
+void bmg_batch_destroy(bmg_batch *bt);
+
 /* Grid size of a system / hierarchy (cells per side). */
 int bmg_system_n(const bmg_system *s);
 int bmg_hierarchy_levels(const bmg_hierarchy *h);

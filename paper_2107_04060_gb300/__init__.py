@@ -74,6 +74,13 @@ _sig = {
     "bmg_launch_count": (C.c_longlong, []),
     "bmg_profile_stop": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "bmg_last_error": (C.c_char_p, []),
+    "bmg_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(KrylovOpts), C.c_int, _vp,
+                                   C.POINTER(_vp)]),
+    "bmg_batch_solve": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(SolveInfo), _vp]),
+    "bmg_batch_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "bmg_batch_trips": (C.c_int, [_vp]),
+    "bmg_batch_kernels_per_trip": (C.c_longlong, [_vp]),
+    "bmg_batch_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -289,6 +296,52 @@ def setup_hierarchy(system: System, smoother: str = "vanka", nu1: int = 1, nu2: 
 
 def vcycle(h: Hierarchy, r, z, stream=None):
     h.vcycle(r, z, stream)
+
+
+class Batch:
+    """Batched FGMRES over independent systems (``bmg_batch_create`` / ``bmg_batch_solve``):
+    one graph launch per solve, the FGMRES state of every instance on the device."""
+
+    def __init__(self, hierarchies, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True,
+                 autotune=True, stream=None):
+        self.hierarchies = list(hierarchies)      # keeps them alive
+        self.count = len(self.hierarchies)
+        arr = (_vp * self.count)(*[h._h for h in self.hierarchies])
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+        self._b = _vp()
+        _check(lib.bmg_batch_create(arr, self.count, C.byref(ko), 1 if autotune else 0,
+                                    _stream(stream), C.byref(self._b)), "bmg_batch_create")
+
+    def solve(self, bs, xs, stream=None):
+        """Solve A_i x_i = b_i for every instance; returns the per-instance info dicts."""
+        assert len(bs) == self.count and len(xs) == self.count
+        pb = (_vp * self.count)(*[_ptr(b) for b in bs])
+        px = (_vp * self.count)(*[_ptr(x) for x in xs])
+        infos = (SolveInfo * self.count)()
+        _check(lib.bmg_batch_solve(self._b, pb, px, infos, _stream(stream)), "bmg_batch_solve")
+        return [_info(i) for i in infos]
+
+    def tile(self, kernel: str, n: int) -> int:
+        return lib.bmg_batch_tile(self._b, PROF[kernel], n)
+
+    @property
+    def trips(self) -> int:
+        return lib.bmg_batch_trips(self._b)
+
+    @property
+    def kernels_per_trip(self) -> int:
+        return lib.bmg_batch_kernels_per_trip(self._b)
+
+    def close(self):
+        if self._b:
+            lib.bmg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 PROF = {"apply": 1, "vanka": 2, "vanka_u": 3, "restrict": 4, "prolong": 5, "coarse": 6, "krylov": 7}

@@ -123,12 +123,53 @@ struct Level {
   float *cinv32 = nullptr;
   // work vectors in the V-cycle precision
   void *rhs = nullptr, *z = nullptr, *t = nullptr, *t2 = nullptr;
+  // Device flag read by every kernel launched for this level (nullptr: always run).  Used by
+  // graph-replayed solves: a kernel whose gate holds 0 returns at once.
+  const int *gate = nullptr;
 };
+
+// Kernel prologue: leave when a gate is present and closed.
+#define BMG_GATE(g) if ((g) != nullptr && *(g) == 0) return
 
 }  // namespace bmg
 
 namespace bmg {
 constexpr int kAdjBlocks = 152 * 8;   // CTAs of the adjoint-gradient reduction
+
+// ---- batched launches: one kernel over several instances of one grid size -------------
+// The per-instance arguments (vectors, coefficients, inverse tables, gate) sit in a device
+// array; blockIdx.z (blockIdx.y for the coarse solve) selects the instance.  FP64 only.
+constexpr int kApplyTiles = 5, kVankaTiles = 4;
+size_t apply_args_bytes();
+void make_apply_args(const Level &L, const double *x, const double *b, double *y, bool residual,
+                     const int *gate, void *dst);
+int launch_apply_batch(const void *d_args, int count, int n, int tile, cudaStream_t st);
+int prepare_apply_batch();
+int default_apply_tile(int n, int count);
+size_t vanka_args_bytes();
+void make_vanka_args(const Level &L, const double *r, double *x, double omega, bool assign,
+                     const int *gate, void *dst);
+int launch_vanka_batch(const void *d_args, int count, int n, int tile, cudaStream_t st);
+int default_vanka_tile(int n, int count);
+struct TransferArgs {          // restriction: fine src -> coarse dst; prolongation: coarse src, fine dst (+=)
+  Grid gf, gc;
+  const double *src;
+  double *dst;
+  const int *gate;
+};
+int launch_restrict_batch(const TransferArgs *d_args, int count, int nf, cudaStream_t st);
+int launch_prolong_batch(const TransferArgs *d_args, int count, int nf, cudaStream_t st);
+struct CoarseArgs {
+  const double *inv;           // [N][N]
+  const int *free_idx;         // [N]
+  const unsigned char *free_mask;   // [vl] 1 on the free DoFs
+  int N;
+  size_t vl;
+  const double *r;
+  double *z;
+  const int *gate;
+};
+int launch_coarse_batch(const CoarseArgs *d_args, int count, int max_free, cudaStream_t st);
 }
 
 struct bmg_system {
@@ -210,7 +251,7 @@ template <typename T>
 int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign);
 // vector kernels
 template <typename T>
-int launch_fill(T *x, T v, size_t n, cudaStream_t st);
+int launch_fill(T *x, T v, size_t n, cudaStream_t st, const int *gate = nullptr);
 int launch_convert_d2f(const double *x, float *y, size_t n, cudaStream_t st);
 int launch_convert_f2d(const float *x, double *y, size_t n, cudaStream_t st);
 int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n,

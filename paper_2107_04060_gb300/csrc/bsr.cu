@@ -124,12 +124,14 @@ struct VankaUArgs {
   T omega;
   int mode;
   int assign;    // mode 1 only: x was zero, write instead of add
+  const int *gate;
 };
 
 // kQX x kQY patches per CTA, NT threads; outputs (kQX - 1) x (kQY - 1).  Same three phases
 // as the 20-DoF sweep: residual gather, (patch, row) solve tasks, weighted gather.
 template <typename T, int kQX, int kQY, int NT>
 __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ VankaUArgs<T> a) {
+  BMG_GATE(a.gate);
   constexpr int NP = kQX * kQY, LD = 9;
   __shared__ T sr[NP * LD];
   __shared__ T sx[NP * LD];
@@ -224,11 +226,13 @@ struct DpArgs {
   const T *r;
   T *d;
   const T *sinv;
+  const int *gate;
   OpCoefs<T> c;
 };
 
 template <typename T>
 __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
+  BMG_GATE(a.gate);
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
   const int cj = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = a.g.n, P = a.g.pitch;
@@ -288,6 +292,7 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
   a.omega = omega;
   a.mode = mode;
   a.assign = assign ? 1 : 0;
+  a.gate = L.gate;
   auto ctas = [&](int px, int py) {
     return (long long)((L.g.pitch + px - 2) / (px - 1)) * ((L.n + 1 + py - 2) / (py - 1));
   };
@@ -319,6 +324,7 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   a.r = r;
   a.d = d;
   a.sinv = (const T *)(f64 ? (const void *)L.sinv64 : (const void *)L.sinv32);
+  a.gate = L.gate;
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
   dim3 b(32, 8), gr((L.n + 31) / 32, (L.n + 7) / 8);
   bsr_dp_kernel<T><<<gr, b, 0, st>>>(a);

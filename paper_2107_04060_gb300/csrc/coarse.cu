@@ -150,7 +150,9 @@ int coarse_setup(Level &L, int *d_flag, cudaStream_t st) {
 // z = A_c^{-1} r on the free DoFs (z's other slots are zeroed first by the caller).
 template <typename T>
 __global__ void coarse_solve_kernel(const T *__restrict__ inv, const int *__restrict__ free_idx,
-                                    int N, const T *__restrict__ r, T *__restrict__ z) {
+                                    int N, const T *__restrict__ r, T *__restrict__ z,
+                                    const int *gate) {
+  BMG_GATE(gate);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= N) return;
@@ -164,15 +166,45 @@ __global__ void coarse_solve_kernel(const T *__restrict__ inv, const int *__rest
 
 template <typename T>
 int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st) {
-  int rc = launch_fill<T>(z, T(0), vec_len_of(L.n), st);
+  int rc = launch_fill<T>(z, T(0), vec_len_of(L.n), st, L.gate);
   if (rc) return rc;
   const T *inv = (const T *)(sizeof(T) == 8 ? (const void *)L.cinv64 : (const void *)L.cinv32);
   const int threads = 256;
   const int blocks = (L.nfree * 32 + threads - 1) / threads;
   { BMG_PROF_BEGIN(BMG_PROF_COARSE, 0, st);
-  coarse_solve_kernel<T><<<blocks, threads, 0, st>>>(inv, L.free_idx, L.nfree, r, z);
+  coarse_solve_kernel<T><<<blocks, threads, 0, st>>>(inv, L.free_idx, L.nfree, r, z, L.gate);
     BMG_PROF_END(st, (double)L.n * L.n); }
   BMG_CHECK_LAUNCH("coarse_solve_kernel");
+  return BMG_OK;
+}
+
+// Batched coarsest solve: blockIdx.y selects the instance; the CTAs of an instance first
+// zero its z outside the free DoFs' rows (blockIdx.x == 0) and then form one row each per
+// warp.  The free DoFs' values never come from the zeroing pass, so the two are independent.
+__global__ void coarse_batch_kernel(const CoarseArgs *__restrict__ args) {
+  const CoarseArgs &a = args[blockIdx.y];
+  BMG_GATE(a.gate);
+  if (blockIdx.x == 0) {
+    for (size_t i = threadIdx.x; i < a.vl; i += blockDim.x)
+      if (!a.free_mask[i]) a.z[i] = 0.0;
+  }
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.N) return;
+  const double *row = a.inv + (size_t)warp * a.N;
+  double acc = 0;
+  for (int c = lane; c < a.N; c += 32) acc = fma(row[c], a.r[a.free_idx[c]], acc);
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (lane == 0) a.z[a.free_idx[warp]] = acc;
+}
+
+int launch_coarse_batch(const CoarseArgs *d_args, int count, int max_free, cudaStream_t st) {
+  if (count <= 0) return BMG_OK;
+  const int threads = 256;
+  dim3 grid((max_free * 32 + threads - 1) / threads, count);
+  coarse_batch_kernel<<<grid, threads, 0, st>>>(d_args);
+  BMG_CHECK_LAUNCH("coarse_batch_kernel");
   return BMG_OK;
 }
 

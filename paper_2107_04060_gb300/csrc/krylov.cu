@@ -6,22 +6,23 @@
 namespace bmg {
 
 template <typename T>
-__global__ void fill_kernel(T *x, T v, size_t n) {
+__global__ void fill_kernel(T *x, T v, size_t n, const int *gate) {
+  BMG_GATE(gate);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     x[i] = v;
 }
 
 template <typename T>
-int launch_fill(T *x, T v, size_t n, cudaStream_t st) {
+int launch_fill(T *x, T v, size_t n, cudaStream_t st, const int *gate) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  fill_kernel<T><<<blocks, 256, 0, st>>>(x, v, n);
+  fill_kernel<T><<<blocks, 256, 0, st>>>(x, v, n, gate);
   BMG_CHECK_LAUNCH("fill_kernel");
   return BMG_OK;
 }
-template int launch_fill<double>(double *, double, size_t, cudaStream_t);
-template int launch_fill<float>(float *, float, size_t, cudaStream_t);
+template int launch_fill<double>(double *, double, size_t, cudaStream_t, const int *);
+template int launch_fill<float>(float *, float, size_t, cudaStream_t, const int *);
 
 __global__ void d2f_kernel(const double *x, float *y, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

@@ -7,6 +7,8 @@
 // phase 2 gathers, for every DoF of the tile, the contributions of its triangles (6 for a
 // vertex, 2 for an edge, 1 for a triangle).  No atomics: the result is deterministic.
 // Constrained displacement slots are ignored on input and written as 0.
+#include <cstring>
+
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
 
@@ -22,6 +24,8 @@ struct ApplyArgs {
   const T *wm;       // [2][6][blk]       (WM == 1)
   size_t bstride;    // batch stride (elements) for batched application
   int residual;
+  int wm_full;       // batched form only: per-instance choice between kinv and wm
+  const int *gate;
   OpCoefs<T> c;
 };
 
@@ -65,7 +69,7 @@ __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T 
 // Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
 // tiles on the coarse levels so that their work spreads over many SMs).
 template <typename T, int WM, int kTX, int kTY, int NT>
-__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+__device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, int bx, int by, size_t boff) {
   constexpr int kEX = kTX + 1, kEY = kTY + 1;
   static_assert(NT >= kTX * kTY, "one thread per output position in phase 2");
   extern __shared__ unsigned char smem_raw[];
@@ -73,10 +77,9 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ Apply
   const Grid g = a.g;
   const int n = g.n, P = g.pitch;
   const size_t blk = g.blk;
-  const size_t boff = (size_t)blockIdx.z * a.bstride;
   const T *x = a.x + boff;
   T *y = a.y + boff;
-  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY;
+  const int i0 = bx * kTX, j0 = by * kTY;
   const int tid = threadIdx.x;
 
   // phase 1: one task per triangle of the tile plus its low-side halo; all lower-left
@@ -166,6 +169,24 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ Apply
   }
 }
 
+template <typename T, int WM, int kTX, int kTY, int NT>
+__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+  BMG_GATE(a.gate);
+  apply_tile<T, WM, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, (size_t)blockIdx.z * a.bstride);
+}
+
+// Batched form: several instances of one grid size in one launch, blockIdx.z selecting the
+// instance whose arguments (coefficients, vectors, gate) are read from a device array.  The
+// FP64 pipe bounds this kernel, so the coefficients' loads from global memory (broadcast,
+// L1-resident) cost little next to the constant-bank operands of the single form.
+template <int kTX, int kTY, int NT>
+__global__ void __launch_bounds__(NT) apply_batch_kernel(const ApplyArgs<double> *__restrict__ args) {
+  const ApplyArgs<double> &a = args[blockIdx.z];
+  BMG_GATE(a.gate);
+  if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, 0);
+  else apply_tile<double, 0, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, 0);
+}
+
 template <typename T, int WM, int TX, int TY, int NT>
 static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   dim3 block(NT);
@@ -211,6 +232,7 @@ int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, in
   a.y = y;
   a.bstride = bstride;
   a.residual = residual ? 1 : 0;
+  a.gate = L.gate;
   const bool f64 = sizeof(T) == 8;
   a.kinv = (const T *)(f64 ? (const void *)L.kinv64 : (const void *)L.kinv32);
   a.wm = (const T *)(f64 ? (const void *)L.wm64 : (const void *)L.wm32);
@@ -227,6 +249,73 @@ template int launch_apply<double>(const Level &, const double *, const double *,
                                   int, size_t, cudaStream_t);
 template int launch_apply<float>(const Level &, const float *, const float *, float *, bool, int,
                                  size_t, cudaStream_t);
+
+// ---- batched application ---------------------------------------------------------------
+size_t apply_args_bytes() { return sizeof(ApplyArgs<double>); }
+
+void make_apply_args(const Level &L, const double *x, const double *b, double *y, bool residual,
+                     const int *gate, void *dst) {
+  ApplyArgs<double> a;
+  a.g = L.g;
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.bstride = 0;
+  a.residual = residual ? 1 : 0;
+  a.wm_full = L.wm_full ? 1 : 0;
+  a.gate = gate;
+  a.kinv = L.kinv64;
+  a.wm = L.wm64;
+  a.c = L.c64;
+  std::memcpy(dst, &a, sizeof(a));
+}
+
+template <int TX, int TY, int NT>
+static int launch_apply_batch_tile(const void *d_args, int count, int n, cudaStream_t st) {
+  const Grid g = grid_of(n);
+  dim3 grid((g.pitch + TX - 1) / TX, (n + 1 + TY - 1) / TY, count);
+  const size_t smem = sizeof(double) * 26 * (TX + 1) * (TY + 1);
+  if (smem > 48 * 1024) {
+    const int rc = prepare_apply_batch();
+    if (rc) return rc;
+  }
+  apply_batch_kernel<TX, TY, NT><<<grid, NT, smem, st>>>((const ApplyArgs<double> *)d_args);
+  BMG_CHECK_LAUNCH("apply_batch_kernel");
+  return BMG_OK;
+}
+
+// Opt-in to the shared memory of the large tiles once, outside any stream capture.
+int prepare_apply_batch() {
+  static bool done = false;
+  if (done) return BMG_OK;
+  BMG_CUDA(cudaFuncSetAttribute(apply_batch_kernel<32, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * 26 * 33 * 9)));
+  done = true;
+  return BMG_OK;
+}
+
+// tile t: 0 = 32 x 8, 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 output positions
+int launch_apply_batch(const void *d_args, int count, int n, int tile, cudaStream_t st) {
+  if (count <= 0) return BMG_OK;
+  switch (tile) {
+    case 0: return launch_apply_batch_tile<32, 8, 256>(d_args, count, n, st);
+    case 1: return launch_apply_batch_tile<16, 8, 128>(d_args, count, n, st);
+    case 2: return launch_apply_batch_tile<8, 8, 128>(d_args, count, n, st);
+    case 3: return launch_apply_batch_tile<8, 4, 96>(d_args, count, n, st);
+    default: return launch_apply_batch_tile<4, 4, 64>(d_args, count, n, st);
+  }
+}
+
+// the single-instance rule: the largest tile that gives every SM about two CTAs
+int default_apply_tile(int n, int count) {
+  static const int tx[kApplyTiles] = {32, 16, 8, 8, 4}, ty[kApplyTiles] = {8, 8, 8, 4, 4};
+  const Grid g = grid_of(n);
+  for (int t = 0; t + 1 < kApplyTiles; ++t) {
+    const long long c = (long long)((g.pitch + tx[t] - 1) / tx[t]) * ((n + 1 + ty[t] - 1) / ty[t]) * count;
+    if (c >= 2 * 152) return t;
+  }
+  return kApplyTiles - 1;
+}
 
 // --------------------------------------------------------------------------------------
 // Galerkin coarsening of the RT0 mass (the coarse-level reading for a per-triangle K):

@@ -29,7 +29,9 @@ int upload_transfer_tables() {
 
 // One thread per (coarse position, DoF type): blockIdx.z is the type.
 template <typename T>
-__global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc) {
+__global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc,
+                                const int *gate) {
+  BMG_GATE(gate);
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int ct = blockIdx.z;
@@ -55,7 +57,9 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
 
 // One thread per (fine position, DoF type): blockIdx.z is the type.
 template <typename T>
-__global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf) {
+__global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf,
+                               const int *gate) {
+  BMG_GATE(gate);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int t = blockIdx.z;
@@ -83,7 +87,7 @@ int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, 
   dim3 block(32, 4);
   dim3 grid((coarse.g.pitch + 31) / 32, (coarse.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_RESTRICT, fine.n, st);
-  restrict_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, rf, rc);
+  restrict_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, rf, rc, fine.gate);
     BMG_PROF_END(st, (double)fine.n * fine.n); }
   BMG_CHECK_LAUNCH("restrict_kernel");
   return BMG_OK;
@@ -95,9 +99,82 @@ int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *x
   dim3 block(32, 4);
   dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_PROLONG, fine.n, st);
-  prolong_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, xc, xf);
+  prolong_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, xc, xf, fine.gate);
     BMG_PROF_END(st, (double)fine.n * fine.n); }
   BMG_CHECK_LAUNCH("prolong_kernel");
+  return BMG_OK;
+}
+
+// ---- batched transfers: blockIdx.z = instance * NBLK + type -----------------------------
+__global__ void restrict_batch_kernel(const TransferArgs *__restrict__ args) {
+  const TransferArgs &a = args[blockIdx.z / NBLK];
+  BMG_GATE(a.gate);
+  const Grid gf = a.gf, gc = a.gc;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ct = blockIdx.z % NBLK;
+  const int nc = gc.n, nf = gf.n;
+  if (I >= gc.pitch || J > nc) return;
+  const size_t o = (size_t)J * gc.pitch + I;
+  double acc = 0;
+  if (I <= nc) {
+    bool m[NBLK];
+    dof_masks(I, J, nc, m);
+    if (m[ct]) {
+      const int ne = c_nres[ct];
+      for (int e = 0; e < ne; ++e) {
+        const StencilEntry se = c_res[ct][e];
+        const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
+        if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
+        acc += se.coef * __ldg(a.src + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
+      }
+    }
+  }
+  a.dst[ct * gc.blk + o] = acc;
+}
+
+__global__ void prolong_batch_kernel(const TransferArgs *__restrict__ args) {
+  const TransferArgs &a = args[blockIdx.z / NBLK];
+  BMG_GATE(a.gate);
+  const Grid gf = a.gf, gc = a.gc;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int t = blockIdx.z % NBLK;
+  const int nf = gf.n, nc = gc.n;
+  if (i > nf || j > nf) return;
+  bool m[NBLK];
+  dof_masks(i, j, nf, m);
+  if (!m[t]) return;
+  const int par = (i & 1) + 2 * (j & 1);
+  const int I0 = i >> 1, J0 = j >> 1;
+  const size_t o = (size_t)j * gf.pitch + i;
+  double acc = 0;
+  const int ne = c_npro[t][par];
+  for (int e = 0; e < ne; ++e) {
+    const StencilEntry se = c_pro[t][par][e];
+    const int I = I0 + se.di, J = J0 + se.dj;
+    if (I < 0 || J < 0 || I > nc || J > nc) continue;
+    acc += se.coef * __ldg(a.src + se.type * gc.blk + (size_t)J * gc.pitch + I);
+  }
+  a.dst[t * gf.blk + o] += acc;
+}
+
+int launch_restrict_batch(const TransferArgs *d_args, int count, int nf, cudaStream_t st) {
+  if (count <= 0) return BMG_OK;
+  const Grid gc = grid_of(nf / 2);
+  dim3 block(32, 4);
+  dim3 grid((gc.pitch + 31) / 32, (gc.n + 1 + 3) / 4, NBLK * count);
+  restrict_batch_kernel<<<grid, block, 0, st>>>(d_args);
+  BMG_CHECK_LAUNCH("restrict_batch_kernel");
+  return BMG_OK;
+}
+
+int launch_prolong_batch(const TransferArgs *d_args, int count, int nf, cudaStream_t st) {
+  if (count <= 0) return BMG_OK;
+  dim3 block(32, 4);
+  dim3 grid((nf + 1 + 31) / 32, (nf + 1 + 3) / 4, NBLK * count);
+  prolong_batch_kernel<<<grid, block, 0, st>>>(d_args);
+  BMG_CHECK_LAUNCH("prolong_batch_kernel");
   return BMG_OK;
 }
 

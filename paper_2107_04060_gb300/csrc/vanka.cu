@@ -21,6 +21,8 @@
 // One CTA computes the local solves of a 32 x 8 block of patches into shared memory and
 // then gathers the weighted corrections of the 31 x 7 positions whose patches it holds:
 // deterministic, no atomics.
+#include <cstring>
+
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
 
@@ -202,10 +204,11 @@ struct VankaSweepArgs {
   int nslots;
   T omega;
   int assign;   // 1: x <- omega M^{-1} r on the free DoFs (x was zero); 0: x += omega M^{-1} r
+  const int *gate;
 };
 
 template <typename T, int kPX, int kPY, int NT>
-__global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+__device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, int by) {
   constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
   __shared__ T sr[NP * LD];
   __shared__ T sx[NP * LD];
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
   __syncthreads();
   const int n = a.g.n, P = a.g.pitch;
   const size_t blk = a.g.blk;
-  const int i0 = blockIdx.x * (kPX - 1), j0 = blockIdx.y * (kPY - 1);
+  const int i0 = bx * (kPX - 1), j0 = by * (kPY - 1);
   const int tid = threadIdx.x;
   // phase 1: residual gather, one patch per thread
   for (int p = tid; p < NP; p += NT) {
@@ -328,6 +331,21 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
   }
 }
 
+template <typename T, int kPX, int kPY, int NT>
+__global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+  BMG_GATE(a.gate);
+  vanka_tile<T, kPX, kPY, NT>(a, blockIdx.x, blockIdx.y);
+}
+
+// Batched form: blockIdx.z selects one of several instances of one grid size; their
+// arguments (vectors, inverse tables, damping, gate) are read from a device array.
+template <int kPX, int kPY, int NT>
+__global__ void __launch_bounds__(NT) vanka_batch_kernel(const VankaSweepArgs<double> *__restrict__ args) {
+  const VankaSweepArgs<double> &a = args[blockIdx.z];
+  BMG_GATE(a.gate);
+  vanka_tile<double, kPX, kPY, NT>(a, blockIdx.x, blockIdx.y);
+}
+
 template <typename T, int PX, int PY, int NT>
 static void launch_vanka_tile(const VankaSweepArgs<T> &a, const Level &L, cudaStream_t st) {
   static_assert(2 * PX * PY * 21 * sizeof(T) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
@@ -350,6 +368,7 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   a.nslots = L.nslots;
   a.omega = omega;
   a.assign = assign ? 1 : 0;
+  a.gate = L.gate;
   BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
   // the largest patch tile that still gives every SM about two CTAs; smaller tiles also
   // spread each patch's rows over more threads
@@ -371,5 +390,54 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
 
 template int launch_vanka_sweep<double>(const Level &, const double *, double *, double, cudaStream_t, bool);
 template int launch_vanka_sweep<float>(const Level &, const float *, float *, float, cudaStream_t, bool);
+
+// ---- batched sweep ---------------------------------------------------------------------
+size_t vanka_args_bytes() { return sizeof(VankaSweepArgs<double>); }
+
+void make_vanka_args(const Level &L, const double *r, double *x, double omega, bool assign,
+                     const int *gate, void *dst) {
+  VankaSweepArgs<double> a;
+  a.g = L.g;
+  a.r = r;
+  a.x = x;
+  a.slot = L.slot;
+  a.inv = L.pinv64;
+  a.nslots = L.nslots;
+  a.omega = omega;
+  a.assign = assign ? 1 : 0;
+  a.gate = gate;
+  std::memcpy(dst, &a, sizeof(a));
+}
+
+template <int PX, int PY, int NT>
+static int launch_vanka_batch_tile(const void *d_args, int count, int n, cudaStream_t st) {
+  static_assert(2 * PX * PY * 21 * sizeof(double) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
+  const Grid g = grid_of(n);
+  dim3 grid((g.pitch + PX - 2) / (PX - 1), (n + 1 + PY - 2) / (PY - 1), count);
+  vanka_batch_kernel<PX, PY, NT><<<grid, NT, 0, st>>>((const VankaSweepArgs<double> *)d_args);
+  BMG_CHECK_LAUNCH("vanka_batch_kernel");
+  return BMG_OK;
+}
+
+// tile t: 0 = 16 x 8, 1 = 8 x 8, 2 = 8 x 4, 3 = 4 x 4 patches
+int launch_vanka_batch(const void *d_args, int count, int n, int tile, cudaStream_t st) {
+  if (count <= 0) return BMG_OK;
+  switch (tile) {
+    case 0: return launch_vanka_batch_tile<16, 8, 256>(d_args, count, n, st);
+    case 1: return launch_vanka_batch_tile<8, 8, 256>(d_args, count, n, st);
+    case 2: return launch_vanka_batch_tile<8, 4, 160>(d_args, count, n, st);
+    default: return launch_vanka_batch_tile<4, 4, 160>(d_args, count, n, st);
+  }
+}
+
+int default_vanka_tile(int n, int count) {
+  static const int px[kVankaTiles] = {16, 8, 8, 4}, py[kVankaTiles] = {8, 8, 4, 4};
+  const Grid g = grid_of(n);
+  for (int t = 0; t + 1 < kVankaTiles; ++t) {
+    const long long c = (long long)((g.pitch + px[t] - 2) / (px[t] - 1)) * ((n + 1 + py[t] - 2) / (py[t] - 1)) * count;
+    if (c >= 2 * 152) return t;
+  }
+  return kVankaTiles - 1;
+}
 
 }  // namespace bmg
