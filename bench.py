@@ -39,8 +39,9 @@ MAXIT = 1000
 # roofline denominators: FP64 FMA pipe (nominal 1.25 TFLOP/s for the GB300; measured
 # 1.20 TFLOP/s with a register FMA loop), HBM from the driver-written measured peaks
 FP64_PEAK_TFLOPS = 1.25
-# algorithmic work per grid cell of the fine-level kernels (derivation in the design doc)
-FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 244 + 26, "vanka_u": 2 * 64 + 10}
+# algorithmic work per grid cell of the fine-level kernels (derivation in the design doc); the
+# operator counts the nonzero products of the element matrices only (156 flops per triangle)
+FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10}
 BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208}
 
 
@@ -324,6 +325,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="print the device time per kernel family of one step and exit")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -432,6 +435,19 @@ def main():
         torch.cuda.synchronize()
         shares[fam] = bmg.profile_stop()
     dominant = max(shares, key=lambda k: shares[k]["ms"])
+    if args.breakdown:
+        # device time per kernel family over all levels, one FP64 step each
+        out = {}
+        for fam in ("apply", "vanka", "vanka_u", "restrict", "prolong", "coarse", "krylov"):
+            bmg.profile_start(fam, 0)
+            one_step("fp64")
+            torch.cuda.synchronize()
+            out[fam] = bmg.profile_stop()
+        ms_step, _, _, _ = timed("fp64", 1)
+        print(json.dumps({"breakdown_ms": {k: round(v["ms"], 3) for k, v in out.items()},
+                          "launches": {k: v["launches"] for k, v in out.items()},
+                          "step_ms": ms_step}))
+        return
 
     # ---- timed region (FP64 V-cycle), clocks sampled meanwhile
     samples, stop = [], threading.Event()

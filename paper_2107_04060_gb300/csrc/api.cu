@@ -192,6 +192,13 @@ static int assemble_impl(int n, double lambda, double mu, const double *K, const
   cudaStream_t st = (cudaStream_t)stream;
   int rc = upload_transfer_tables();
   if (rc) return rc;
+  static const bool pattern_ok = [] {
+    std::string why;
+    const bool ok = verify_elem_nonzeros(&why);
+    if (!ok) set_error("element integrals do not have the compiled sparsity: " + why);
+    return ok;
+  }();
+  if (!pattern_ok) return BMG_ERR_ARG;
   bmg_system *s = new bmg_system();
   s->n = n;
   s->prm = PhysParams{lambda, mu, tau, alpha, inv_M};
@@ -305,8 +312,8 @@ static int setup_patches(bmg_hierarchy *h, Level &L, int psize, double p_shift,
   BMG_CUDA(cudaMalloc(&L.slot, sizeof(int) * slot.size()));
   BMG_CUDA(cudaMalloc(&d_ri, sizeof(int) * nrep));
   BMG_CUDA(cudaMalloc(&d_rj, sizeof(int) * nrep));
-  BMG_CUDA(cudaMalloc(&L.pinv64, sizeof(double) * (size_t)psize * psize * nrep));
-  BMG_CUDA(cudaMalloc(&L.pinv32, sizeof(float) * (size_t)psize * psize * nrep));
+  BMG_CUDA(cudaMalloc(&L.pinv64, sizeof(double) * (size_t)patch_entries(psize) * nrep));
+  BMG_CUDA(cudaMalloc(&L.pinv32, sizeof(float) * (size_t)patch_entries(psize) * nrep));
   BMG_CUDA(cudaMemcpyAsync(L.slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice, st));
   BMG_CUDA(cudaMemcpyAsync(d_ri, ri.data(), sizeof(int) * nrep, cudaMemcpyHostToDevice, st));
   BMG_CUDA(cudaMemcpyAsync(d_rj, rj.data(), sizeof(int) * nrep, cudaMemcpyHostToDevice, st));

@@ -60,6 +60,18 @@ struct OpCoefs {
   T pp;         // (1/M) |T|
 };
 
+// Structural nonzeros of the element integrals on the two reference right triangles (the
+// same pattern for L and U; stiffness-type integrals are scale-free in 2D, so the pattern
+// holds for every h): bit b of row a set <=> Aeps[a][b] != 0; the g and unit-mass patterns.
+// verify_elem_nonzeros() checks them against element_integrals() before the first assembly.
+constexpr unsigned short kAepsRows[9] = {0x0DF, 0x0C3, 0x05D, 0x17D, 0x05D, 0x168, 0x1FF, 0x1C3, 0x1E8};
+constexpr unsigned short kGNonzero = 0x1EB;          // g[2] = g[4] = 0
+constexpr unsigned short kMwRows[3] = {0x1, 0x6, 0x6};
+__host__ __device__ constexpr bool aeps_nonzero(int a, int b) { return (kAepsRows[a] >> b) & 1; }
+__host__ __device__ constexpr bool g_nonzero(int k) { return (kGNonzero >> k) & 1; }
+__host__ __device__ constexpr bool mw_nonzero(int a, int b) { return (kMwRows[a] >> b) & 1; }
+bool verify_elem_nonzeros(std::string *why);
+
 struct PhysParams {
   double lambda, mu, tau, alpha, inv_M;
 };
@@ -108,7 +120,8 @@ struct Level {
   int nslots = 0;
   int *slot = nullptr;         // [(n+1) * (n+1)] patch -> inverse slot
   int psize = 0;               // 20 (Vanka) or 8 (BSR displacement patches)
-  double *pinv64 = nullptr;    // [psize*psize][nslots]
+  double *pinv64 = nullptr;    // [patch_entries(psize)][nslots]: psize 20 packed symmetric
+                               // (upper triangle, row-major), psize 8 full row-major
   float *pinv32 = nullptr;
   // BSR data
   double *dinv64 = nullptr;    // [3][blk] 1 / (tau D_w) per edge family
@@ -127,6 +140,10 @@ struct Level {
   // graph-replayed solves: a kernel whose gate holds 0 returns at once.
   const int *gate = nullptr;
 };
+
+// Stored entries of one patch inverse: the 20 x 20 Vanka inverse is symmetric (the patch
+// matrix V A V^T of the symmetric A) and kept as its upper triangle; the 8 x 8 one is full.
+inline int patch_entries(int psize) { return psize == 20 ? 210 : psize * psize; }
 
 // Kernel prologue: leave when a gate is present and closed.
 #define BMG_GATE(g) if ((g) != nullptr && *(g) == 0) return

@@ -327,7 +327,9 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   a.gate = L.gate;
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
   dim3 b(32, 8), gr((L.n + 31) / 32, (L.n + 7) / 8);
+  { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
   bsr_dp_kernel<T><<<gr, b, 0, st>>>(a);
+    BMG_PROF_END(st, 0.0); }
   BMG_CHECK_LAUNCH("bsr_dp_kernel");
   // r_y - B^T dp: the residual of (0, 0, dp) against r (its p part is not used)
   if ((rc = launch_apply<T>(L, d, r, ry, true, 1, 0, st))) return rc;

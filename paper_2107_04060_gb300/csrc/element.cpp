@@ -6,6 +6,7 @@
 // n_v = (1,0), n_d = (1,1)/sqrt2; RT0 psi_e with psi_e . n_e = 1 on e; P0 indicators.
 // Every integrand is a polynomial of degree <= 2, integrated exactly by the three-point
 // edge-midpoint rule.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -149,6 +150,38 @@ void element_integrals(double h, ElemIntegrals *out) {
       }
     }
   }
+}
+
+bool verify_elem_nonzeros(std::string *why) {
+  ElemIntegrals e;
+  element_integrals(1.0, &e);
+  for (int o = 0; o < 2; ++o) {
+    double amax = 0.0, gmax = 0.0, mmax = 0.0;
+    for (int a = 0; a < 9; ++a) {
+      gmax = std::max(gmax, std::fabs(e.g[o][a]));
+      for (int b = 0; b < 9; ++b) amax = std::max(amax, std::fabs(e.Aeps[o][a][b]));
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) mmax = std::max(mmax, std::fabs(e.Mw[o][a][b]));
+    for (int a = 0; a < 9; ++a) {
+      if (!g_nonzero(a) && std::fabs(e.g[o][a]) > 1e-13 * gmax) {
+        *why = "div-integral pattern";
+        return false;
+      }
+      for (int b = 0; b < 9; ++b)
+        if (!aeps_nonzero(a, b) && std::fabs(e.Aeps[o][a][b]) > 1e-13 * amax) {
+          *why = "strain-matrix pattern";
+          return false;
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (!mw_nonzero(a, b) && std::fabs(e.Mw[o][a][b]) > 1e-13 * mmax) {
+          *why = "RT0 mass pattern";
+          return false;
+        }
+  }
+  return true;
 }
 
 void make_coefs(const PhysParams &p, int n, OpCoefs<double> *c64, OpCoefs<float> *c32) {

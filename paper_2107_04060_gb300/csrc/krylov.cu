@@ -108,9 +108,11 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partial, int n
 // out[0..k-1] = V_q . w, out[k] = w . w  (deterministic two-stage reduction)
 int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                 int nblocks, double *out, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   dots_kernel<<<nblocks, 256, 0, st>>>(V, ldv, k, w, n, partial);
   BMG_CHECK_LAUNCH("dots_kernel");
   reduce_partials_kernel<<<k + 1, 256, 0, st>>>(partial, nblocks, k + 1, out);
+  BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
 }
@@ -126,7 +128,9 @@ __global__ void update_kernel(double *__restrict__ w, const double *__restrict__
 }
 int launch_update(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                   cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   update_kernel<<<152 * 8, 256, 0, st>>>(w, V, ldv, k, h, n);
+  BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("update_kernel");
   return BMG_OK;
 }
@@ -190,10 +194,12 @@ __global__ void __launch_bounds__(256) update_dots_kernel(double *__restrict__ w
 // out[0] = w_new . w_new when dots == 0.
 int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                        int dots, double *partial, int nblocks, double *out, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   update_dots_kernel<<<nblocks, 256, 0, st>>>(w, V, ldv, k, h, n, dots, partial);
   BMG_CHECK_LAUNCH("update_dots_kernel");
   const int cnt = dots ? k + 1 : 1;
   reduce_partials_kernel<<<cnt, 256, 0, st>>>(partial, nblocks, cnt, out);
+  BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
 }
@@ -206,7 +212,9 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
     v[i] = w[i] * d;
 }
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   scale_kernel<<<152 * 8, 256, 0, st>>>(w, v, s, n);
+  BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("scale_kernel");
   return BMG_OK;
 }
@@ -222,7 +230,9 @@ __global__ void axpy_multi_kernel(double *__restrict__ x, const double *__restri
 }
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y, size_t n,
                       cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   axpy_multi_kernel<<<152 * 8, 256, 0, st>>>(x, Z, ldz, k, y, n);
+  BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("axpy_multi_kernel");
   return BMG_OK;
 }

@@ -8,6 +8,8 @@
 // vertex, 2 for an edge, 1 for a triangle).  No atomics: the result is deterministic.
 // Constrained displacement slots are ignored on input and written as 0.
 #include <cstring>
+#include <type_traits>
+#include <utility>
 
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
@@ -30,33 +32,53 @@ struct ApplyArgs {
 };
 
 
-// Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1, so that the body
+// can branch on the index with `if constexpr`.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).  Products with the
+// structural zeros of the element matrices are not formed (Aeps 30 of 81, g 2 of 9, the
+// unit RT0 mass 4 of 9; see kElemNonzeros).
 template <typename T, int WM>
 __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T u[9],
                                             const T w[3], T p, T kinv, const T *wmT,
                                             T *yl) {
   T gu = 0;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) gu = fma(c.g[o][k], u[k], gu);
+  static_for<9>([&](auto k_) {
+    constexpr int k = decltype(k_)::value;
+    if constexpr (g_nonzero(k)) gu = fma(c.g[o][k], u[k], gu);
+  });
   const T s = c.lam_area * gu - c.alpha * p;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    T acc = c.g[o][a] * s;
-#pragma unroll
-    for (int b = 0; b < 9; ++b) acc = fma(c.A[o][a * 9 + b], u[b], acc);
+  static_for<9>([&](auto a_) {
+    constexpr int a = decltype(a_)::value;
+    T acc = 0;
+    if constexpr (g_nonzero(a)) acc = c.g[o][a] * s;
+    static_for<9>([&](auto b_) {
+      constexpr int b = decltype(b_)::value;
+      if constexpr (aeps_nonzero(a, b)) acc = fma(c.A[o][a * 9 + b], u[b], acc);
+    });
     yl[a] = acc;
-  }
+  });
   T dww = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) dww = fma(c.dw[o][k], w[k], dww);
   if (WM == 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    static_for<3>([&](auto a_) {
+      constexpr int a = decltype(a_)::value;
       T acc = 0;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) acc = fma(c.M1[o][a * 3 + b], w[b], acc);
+      static_for<3>([&](auto b_) {
+        constexpr int b = decltype(b_)::value;
+        if constexpr (mw_nonzero(a, b)) acc = fma(c.M1[o][a * 3 + b], w[b], acc);
+      });
       yl[9 + a] = kinv * acc - c.dw[o][a] * p;
-    }
+    });
   } else {
     // symmetric 3x3: (00, 01, 02, 11, 12, 22)
     yl[9] = wmT[0] * w[0] + wmT[1] * w[1] + wmT[2] * w[2] - c.dw[o][0] * p;

@@ -55,6 +55,17 @@ __device__ __forceinline__ void patch_active(int vi, int vj, int n, bool act[20]
   }
 }
 
+// Packed position of entry (r, c) of a symmetric 20 x 20 matrix (upper triangle, row-major).
+__host__ __device__ __forceinline__ int sym20(int r, int c) {
+  const int a = r < c ? r : c, b = r < c ? c : r;
+  return a * 20 - (a * (a - 1)) / 2 + (b - a);
+}
+
+// Entry c of row r: for c >= r it is (r, c), at base(r) + c; for c < r it is (c, r), at
+// base(c) + r, with base(a) = sym20(a, 0) - a = 19 a - a (a - 1) / 2 (a compile-time
+// constant when c is an unrolled loop index).
+__device__ __forceinline__ int sym20_row_base(int r) { return r * 19 - (r * (r - 1)) / 2; }
+
 struct VankaSetupArgs {
   Grid g;
   const double *kinv;
@@ -158,12 +169,23 @@ __global__ void __launch_bounds__(64) vanka_setup_kernel(const __grid_constant__
     }
   }
   if (!ok) atomicOr(a.flag, 1);
-  for (int r = 0; r < ps; ++r)
-    for (int c = 0; c < ps; ++c) {
-      const double v = ok ? Inv[r][c] : 0.0;
-      a.inv64[(size_t)(r * ps + c) * a.nrep + s] = v;
-      a.inv32[(size_t)(r * ps + c) * a.nrep + s] = (float)v;
-    }
+  if (ps == 20) {
+    // symmetric: the upper triangle of (Inv + Inv^T) / 2, row-major
+    for (int r = 0; r < 20; ++r)
+      for (int c = r; c < 20; ++c) {
+        const double v = ok ? 0.5 * (Inv[r][c] + Inv[c][r]) : 0.0;
+        const size_t e = (size_t)sym20(r, c);
+        a.inv64[e * a.nrep + s] = v;
+        a.inv32[e * a.nrep + s] = (float)v;
+      }
+  } else {
+    for (int r = 0; r < ps; ++r)
+      for (int c = 0; c < ps; ++c) {
+        const double v = ok ? Inv[r][c] : 0.0;
+        a.inv64[(size_t)(r * ps + c) * a.nrep + s] = v;
+        a.inv32[(size_t)(r * ps + c) * a.nrep + s] = (float)v;
+      }
+  }
 }
 
 int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
@@ -268,8 +290,12 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
     if (tid < NG * 20) {
       const int row = tid % 20, grp = tid / 20;
       T irow[20];
+      const int rb = sym20_row_base(row);
 #pragma unroll
-      for (int c = 0; c < 20; ++c) irow[c] = a.inv[(size_t)(row * 20 + c) * ld];
+      for (int c = 0; c < 20; ++c) {
+        const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
+        irow[c] = a.inv[(size_t)e * ld];
+      }
       for (int p = grp; p < NP; p += NG) {
         const T *rl = sr + p * LD;
         T acc = 0;
@@ -283,11 +309,15 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
     // take consecutive patches of one row, so their inverse loads coalesce (or broadcast)
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
-      const T *inv = a.inv + ss[p] + (size_t)(row * 20) * ld;
+      const T *inv = a.inv + ss[p];
+      const int rb = sym20_row_base(row);
       const T *rl = sr + p * LD;
       T acc = 0;
 #pragma unroll
-      for (int c = 0; c < 20; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
+      for (int c = 0; c < 20; ++c) {
+        const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
+        acc = fma(inv[(size_t)e * ld], rl[c], acc);
+      }
       sx[p * LD + row] = acc;
     }
   }
