@@ -1,6 +1,7 @@
 // C ABI of the library (include/biotmg.h): systems, hierarchies, the V-cycle and FGMRES.
 // Host code only orchestrates: every arithmetic step of assembly, relaxation, transfer,
 // coarse solve and Krylov iteration runs in this library's kernels.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -327,6 +328,92 @@ static int setup_patches(bmg_hierarchy *h, Level &L, int psize, double p_shift,
   return BMG_OK;
 }
 
+// ---- tile tuning ---------------------------------------------------------------------
+// Times every candidate tile of a level's operator and smoother launches (on the level's own
+// work vectors) and keeps the fastest.  The results do not depend on the tile: every output
+// value is formed by the same arithmetic whichever tile holds it.
+template <typename F>
+static int time_min(F &&launch, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float *ms) {
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    BMG_CUDA(cudaEventRecord(e0, st));
+    int rc = launch();
+    if (rc) return rc;
+    BMG_CUDA(cudaEventRecord(e1, st));
+    BMG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    BMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    if (rep > 0) best = std::min(best, t);        // the first launch warms up
+  }
+  *ms = best;
+  return BMG_OK;
+}
+
+template <typename F>
+static int pick_tile(int *slot, int first, int last, F &&launch, cudaEvent_t e0, cudaEvent_t e1,
+                     cudaStream_t st) {
+  float best = 1e30f;
+  int best_t = -1;
+  for (int t = first; t <= last; ++t) {
+    *slot = t;
+    float ms;
+    int rc = time_min(launch, e0, e1, st, &ms);
+    if (rc) {
+      *slot = -1;
+      return rc;
+    }
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  *slot = best_t;
+  return BMG_OK;
+}
+
+template <typename T>
+static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
+  T *z = (T *)L.z, *t = (T *)L.t;
+  const T *r = (const T *)L.rhs;
+  int rc = pick_tile(&L.tile_apply, 0, 4, [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); },
+                     e0, e1, st);
+  if (rc) return rc;
+  if (h->opts.smoother == BMG_VANKA)
+    return pick_tile(&L.tile_vanka, sizeof(T) == 4 ? 0 : 1, 4,
+                     [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
+  return pick_tile(&L.tile_vanka_u, 0, 4,
+                   [&] { return launch_bsr_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
+}
+
+static int tune_hierarchy(bmg_hierarchy *h, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  BMG_CUDA(cudaEventCreate(&e0));
+  BMG_CUDA(cudaEventCreate(&e1));
+  int rc = BMG_OK;
+  const bool fp32 = h->opts.precision == BMG_FP32;
+  for (size_t l = 0; l + 1 < h->levels.size() && !rc; ++l)
+    rc = fp32 ? tune_level<float>(h, h->levels[l], e0, e1, st) : tune_level<double>(h, h->levels[l], e0, e1, st);
+  // the FP64 fine-level operator of FGMRES (its own FP64 scratch vectors)
+  if (!rc) {
+    Level &F = h->fine_op;
+    const size_t vl = vec_len_of(F.n);
+    double *a = nullptr, *b = nullptr;
+    if (cudaMalloc(&a, sizeof(double) * vl) != cudaSuccess || cudaMalloc(&b, sizeof(double) * vl) != cudaSuccess) {
+      rc = cuda_fail(cudaErrorMemoryAllocation, "tuning vectors");
+    } else {
+      cudaMemsetAsync(a, 0, sizeof(double) * vl, st);
+      rc = pick_tile(&F.tile_apply, 0, 4, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
+                     e0, e1, st);
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(a);
+    cudaFree(b);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, void *stream,
                                    bmg_hierarchy **out) {
   if (!out) return arg_error("bmg_setup_hierarchy: out is NULL");
@@ -421,6 +508,9 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
   }
   int rc = coarse_setup(h->levels.back(), h->d_flag, st);
   if (rc) return fail(rc);
+  h->fine_op = s->fine;
+  h->fine_op.owns_coefs = false;
+  if ((rc = tune_hierarchy(h, st))) return fail(rc);
   int hflag = 0;
   cudaError_t e = cudaMemcpyAsync(&hflag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -566,7 +656,7 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
   double est = 1.0;
   for (;;) {
     // true residual
-    if ((rc = launch_apply<double>(s->fine, x, b, h->r, true, 1, 0, st))) return rc;
+    if ((rc = launch_apply<double>(h->fine_op, x, b, h->r, true, 1, 0, st))) return rc;
     if ((rc = launch_dots(nullptr, vl, 0, h->r, vl, h->partial, kDotBlocks, h->dres, st))) return rc;
     BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double), cudaMemcpyDeviceToHost, st));
     BMG_CUDA(cudaStreamSynchronize(st));
@@ -588,7 +678,7 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       double *vj = h->V + (size_t)j * ldv;
       double *zj = h->Z + (size_t)j * ldv;
       if ((rc = vcycle_any(h, vj, zj, st))) return rc;
-      if ((rc = launch_apply<double>(s->fine, zj, nullptr, h->w, false, 1, 0, st))) return rc;
+      if ((rc = launch_apply<double>(h->fine_op, zj, nullptr, h->w, false, 1, 0, st))) return rc;
       double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
       // CGS2: h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with ||w||^2
       if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d1, st))) return rc;

@@ -136,6 +136,9 @@ struct Level {
   float *cinv32 = nullptr;
   // work vectors in the V-cycle precision
   void *rhs = nullptr, *z = nullptr, *t = nullptr, *t2 = nullptr;
+  // Tile shape of the operator / Vanka / displacement-Vanka launches on this level, chosen by
+  // timing at setup (index into each kernel's candidate list; -1: the CTA-count rule).
+  int tile_apply = -1, tile_vanka = -1, tile_vanka_u = -1;
   // Device flag read by every kernel launched for this level (nullptr: always run).  Used by
   // graph-replayed solves: a kernel whose gate holds 0 returns at once.
   const int *gate = nullptr;
@@ -203,6 +206,8 @@ struct bmg_hierarchy {
   bmg_mg_opts opts;
   std::vector<bmg::Level> levels;
   int *d_flag = nullptr;       // device error flag (singular pivots)
+  bmg::Level fine_op;          // the system's fine level with the FP64 operator tile tuned
+                               // for this device (FGMRES matvec and true residual)
   // FGMRES workspace (FP64)
   int m_alloc = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *xb = nullptr;

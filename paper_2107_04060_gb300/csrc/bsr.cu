@@ -298,11 +298,19 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
   };
   BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
   const long long want = 2 * 152;
-  if (ctas(32, 8) >= want) launch_vanka_u_tile<T, 32, 8, 256>(a, L, st);
-  else if (ctas(16, 8) >= want) launch_vanka_u_tile<T, 16, 8, 256>(a, L, st);
-  else if (ctas(8, 8) >= want) launch_vanka_u_tile<T, 8, 8, 128>(a, L, st);
-  else if (ctas(8, 4) >= want) launch_vanka_u_tile<T, 8, 4, 128>(a, L, st);
-  else launch_vanka_u_tile<T, 4, 4, 64>(a, L, st);
+  switch (L.tile_vanka_u) {          // tuned at setup
+    case 0: launch_vanka_u_tile<T, 32, 8, 256>(a, L, st); break;
+    case 1: launch_vanka_u_tile<T, 16, 8, 256>(a, L, st); break;
+    case 2: launch_vanka_u_tile<T, 8, 8, 128>(a, L, st); break;
+    case 3: launch_vanka_u_tile<T, 8, 4, 128>(a, L, st); break;
+    case 4: launch_vanka_u_tile<T, 4, 4, 64>(a, L, st); break;
+    default:
+      if (ctas(32, 8) >= want) launch_vanka_u_tile<T, 32, 8, 256>(a, L, st);
+      else if (ctas(16, 8) >= want) launch_vanka_u_tile<T, 16, 8, 256>(a, L, st);
+      else if (ctas(8, 8) >= want) launch_vanka_u_tile<T, 8, 8, 128>(a, L, st);
+      else if (ctas(8, 4) >= want) launch_vanka_u_tile<T, 8, 4, 128>(a, L, st);
+      else launch_vanka_u_tile<T, 4, 4, 64>(a, L, st);
+  }
   BMG_PROF_END(st, (double)L.n * L.n);
   BMG_CHECK_LAUNCH("vanka_u_kernel");
   return BMG_OK;

@@ -233,6 +233,14 @@ static long long ctas_for(const Level &L, int tx, int ty, int batch) {
 
 template <typename T, int WM>
 static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
+  switch (L.tile_apply) {            // tuned at setup (same candidates as the batched form)
+    case 0: return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
+    case 1: return launch_apply_tile<T, WM, 16, 8, 128>(a, L, batch, st);
+    case 2: return launch_apply_tile<T, WM, 8, 8, 128>(a, L, batch, st);
+    case 3: return launch_apply_tile<T, WM, 8, 4, 96>(a, L, batch, st);
+    case 4: return launch_apply_tile<T, WM, 4, 4, 64>(a, L, batch, st);
+    default: break;
+  }
   // the largest tile that still gives every SM about two CTAs
   const long long want = 2 * 152;
   // small tiles get more threads than positions so that the triangle products (phase 1)

@@ -404,9 +404,21 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   // spread each patch's rows over more threads
   // (two 21-wide shared arrays per patch: 32 x 8 patches fit the 48 KB static limit in FP32 only)
   const long long want = 2 * 152;
-  bool done = false;
+  bool done = true;
+  // tuned at setup: 0 = 32 x 8 (FP32 only), 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 patches
+  switch (L.tile_vanka) {
+    case 0:
+      if constexpr (sizeof(T) == 4) launch_vanka_tile<T, 32, 8, 256>(a, L, st);
+      else launch_vanka_tile<T, 16, 8, 256>(a, L, st);
+      break;
+    case 1: launch_vanka_tile<T, 16, 8, 256>(a, L, st); break;
+    case 2: launch_vanka_tile<T, 8, 8, 256>(a, L, st); break;
+    case 3: launch_vanka_tile<T, 8, 4, 160>(a, L, st); break;
+    case 4: launch_vanka_tile<T, 4, 4, 160>(a, L, st); break;
+    default: done = false;
+  }
   if constexpr (sizeof(T) == 4) {
-    if (vanka_ctas(L, 32, 8) >= want) { launch_vanka_tile<T, 32, 8, 256>(a, L, st); done = true; }
+    if (!done && vanka_ctas(L, 32, 8) >= want) { launch_vanka_tile<T, 32, 8, 256>(a, L, st); done = true; }
   }
   if (done) {
   } else if (vanka_ctas(L, 16, 8) >= want) launch_vanka_tile<T, 16, 8, 256>(a, L, st);
