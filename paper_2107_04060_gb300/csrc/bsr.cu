@@ -5,8 +5,8 @@
 //   S  ~= (1/M + alpha^2 / (lambda + 2 mu / d)) M_p + tau B_w D_w^{-1} B_w^T   (d = 2)
 //   z   = F^{-1} r_y;   dp = omega_J diag(S)^{-1} (B z - r_p);   dy = F^{-1}(r_y - B^T dp)
 //   x  <- x + omega (dy, dp)
-// Kernels: (1) z = F^{-1} r_y; (2) dp per triangle; (3) r_y - B^T dp through the
-// matrix-free operator applied to (0, 0, dp); (4) dy = F^{-1}(...) fused with the update.
+// Kernels: (1) z = F^{-1} r_y; (2) dp per triangle; (3) r_y - B^T dp from the coupling
+// terms of the element products alone; (4) dy = F^{-1}(...) fused with the update.
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
 
@@ -269,6 +269,61 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
   }
 }
 
+// r_y - B^T dp on the displacement and flux DoFs (the p blocks are not written): with
+// A (0, 0, dp) = (-alpha g_T dp_T, -tau dw_T dp_T, .) per triangle (the operator's element
+// product at u = w = 0), r_u + alpha sum_T g_T dp_T and r_w + sum_T tau dw_T dp_T over the
+// triangles that hold each DoF (6 for a vertex, 2 for an edge).  Constrained slots get 0.
+template <typename T>
+struct RyArgs {
+  Grid g;
+  const T *r;
+  const T *d;    // dp in the p blocks
+  T *ry;
+  const int *gate;
+  T ag[2][9];    // alpha * g
+  T dw[2][3];    // tau * dw
+};
+
+template <typename T>
+__global__ void bsr_ry_kernel(const __grid_constant__ RyArgs<T> a) {
+  BMG_GATE(a.gate);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = a.g.n, P = a.g.pitch;
+  const size_t blk = a.g.blk;
+  if (i >= P || j > n) return;
+  const size_t o = (size_t)j * P + i;
+  if (i > n) {                                       // padding columns
+#pragma unroll
+    for (int k = UX; k <= WD; ++k) a.ry[k * blk + o] = T(0);
+    return;
+  }
+  auto dp = [&](int b, int ci, int cj) -> T {        // dp of L (b = PL) or U (b = PU) at cell (ci, cj)
+    return (ci >= 0 && cj >= 0 && ci < n && cj < n) ? a.d[b * blk + (size_t)cj * P + ci] : T(0);
+  };
+  const T pL = dp(PL, i, j), pLw = dp(PL, i - 1, j), pLs = dp(PL, i, j - 1);
+  const T pUw = dp(PU, i - 1, j), pUsw = dp(PU, i - 1, j - 1), pUs = dp(PU, i, j - 1);
+  const T pU = dp(PU, i, j);
+  // vertex (i, j): local vertex 0 of L(i,j) and U(i-1,j-1), 1 of L(i-1,j) and U(i,j-1),
+  // 2 of L(i,j-1) and U(i-1,j)
+  T v[8];
+  v[UX] = a.ag[0][0] * pL + a.ag[0][1] * pLw + a.ag[0][2] * pLs +
+          a.ag[1][2] * pUw + a.ag[1][0] * pUsw + a.ag[1][1] * pUs;
+  v[UY] = a.ag[0][3] * pL + a.ag[0][4] * pLw + a.ag[0][5] * pLs +
+          a.ag[1][5] * pUw + a.ag[1][3] * pUsw + a.ag[1][4] * pUs;
+  // h(i,j): e2 of L(i,j) and U(i,j-1); v(i,j): e1 of L(i,j) and U(i-1,j); d(i,j): e0 of both
+  v[BH] = a.ag[0][8] * pL + a.ag[1][8] * pUs;
+  v[BV] = a.ag[0][7] * pL + a.ag[1][7] * pUw;
+  v[BD] = a.ag[0][6] * pL + a.ag[1][6] * pU;
+  v[WH] = a.dw[0][2] * pL + a.dw[1][2] * pUs;
+  v[WV] = a.dw[0][1] * pL + a.dw[1][1] * pUw;
+  v[WD] = a.dw[0][0] * pL + a.dw[1][0] * pU;
+  bool m[NBLK];
+  dof_masks(i, j, n, m);
+#pragma unroll
+  for (int k = UX; k <= WD; ++k) a.ry[k * blk + o] = m[k] ? a.r[k * blk + o] + v[k] : T(0);
+}
+
 template <typename T, int QX, int QY, int NT>
 static void launch_vanka_u_tile(const VankaUArgs<T> &a, const Level &L, cudaStream_t st) {
   dim3 grid((L.g.pitch + QX - 2) / (QX - 1), (L.n + 1 + QY - 2) / (QY - 1));
@@ -339,8 +394,22 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   bsr_dp_kernel<T><<<gr, b, 0, st>>>(a);
     BMG_PROF_END(st, 0.0); }
   BMG_CHECK_LAUNCH("bsr_dp_kernel");
-  // r_y - B^T dp: the residual of (0, 0, dp) against r (its p part is not used)
-  if ((rc = launch_apply<T>(L, d, r, ry, true, 1, 0, st))) return rc;
+  // r_y - B^T dp on the u and w blocks
+  RyArgs<T> ra;
+  ra.g = L.g;
+  ra.r = r;
+  ra.d = d;
+  ra.ry = ry;
+  ra.gate = L.gate;
+  for (int o = 0; o < 2; ++o) {
+    for (int k = 0; k < 9; ++k) ra.ag[o][k] = a.c.alpha * a.c.g[o][k];
+    for (int k = 0; k < 3; ++k) ra.dw[o][k] = a.c.dw[o][k];
+  }
+  dim3 rb(32, 8), rg((L.g.pitch + 31) / 32, (L.n + 1 + 7) / 8);
+  { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
+  bsr_ry_kernel<T><<<rg, rb, 0, st>>>(ra);
+    BMG_PROF_END(st, 0.0); }
+  BMG_CHECK_LAUNCH("bsr_ry_kernel");
   return launch_vanka_u<T>(L, ry, nullptr, x, d, omega, 1, assign, st);
 }
 
