@@ -325,7 +325,7 @@ static int setup_patches(bmg_hierarchy *h, Level &L, int psize, double p_shift,
   cudaFree(d_rj);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "vanka setup");
-  return BMG_OK;
+  return psize == 20 ? vanka_klein_setup(L, st) : BMG_OK;
 }
 
 // ---- tile tuning ---------------------------------------------------------------------

@@ -120,6 +120,11 @@ struct Level {
   int nslots = 0;
   int *slot = nullptr;         // [(n+1) * (n+1)] patch -> inverse slot
   int psize = 0;               // 20 (Vanka) or 8 (BSR displacement patches)
+  // uniform coefficients: the shared interior inverse in the symmetry-adapted basis (blocks
+  // of 4, 5, 7, 4; row k holds block entries 0..size-1), verified against the dense inverse
+  bool klein = false;
+  double kb64[20][7] = {};
+  float kb32[20][7] = {};
   double *pinv64 = nullptr;    // [patch_entries(psize)][nslots]: psize 20 packed symmetric
                                // (upper triangle, row-major), psize 8 full row-major
   float *pinv32 = nullptr;
@@ -254,6 +259,7 @@ namespace bmg {
 template <typename T>
 int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, int batch,
                  size_t bstride, cudaStream_t st);
+int vanka_klein_setup(Level &L, cudaStream_t st);
 int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
                        double p_shift_area, int psize, int *d_flag, cudaStream_t st);
 template <typename T>

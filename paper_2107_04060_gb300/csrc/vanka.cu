@@ -21,6 +21,7 @@
 // One CTA computes the local solves of a 32 x 8 block of patches into shared memory and
 // then gathers the weighted corrections of the 31 x 7 positions whose patches it holds:
 // deterministic, no atomics.
+#include <cmath>
 #include <cstring>
 
 #include "bmg_internal.h"
@@ -53,6 +54,70 @@ __device__ __forceinline__ void patch_active(int vi, int vj, int n, bool act[20]
     const int ci = vi + c_tdi[t], cj = vj + c_tdj[t];
     act[14 + t] = ci >= 0 && cj >= 0 && ci < n && cj < n;
   }
+}
+
+// ---- symmetry-adapted interior patch ---------------------------------------------------
+// With uniform coefficients the matrix of an interior patch commutes with the signed slot
+// permutations of the three symmetries of the triangulation around the vertex: the point
+// reflection (ux, uy, bubble and flux DoFs change sign, E0<->E2, E1<->E3, E4<->E5, L(i,j) <->
+// U(i-1,j-1), L(i-1,j) <-> U(i,j-1), L(i,j-1) <-> U(i-1,j)) and the reflections in the two
+// diagonals through the vertex (the x <-> y one maps ux <-> uy, E0<->E1, E2<->E3, E4<->E5,
+// L(i-1,j) <-> L(i,j-1), U(i-1,j) <-> U(i,j-1), with no sign change: the global normals
+// (0,1), (1,0), (1,1)/sqrt2 map onto each other).  The four characters of this group split
+// the 20 slots into blocks of 4, 5, 7 and 4: in the basis U (columns of +-1 entries, one per
+// character and orbit) the inverse is block diagonal, x = U B U^T r with
+// B = diag(1/d) U^T A^{-1} U diag(1/d), d_k = |U_k|^2.  klein_fwd forms U^T r and klein_inv
+// forms U x' with butterflies of additions (32 each), so a patch solve costs 106 FMAs plus 64
+// additions instead of 400 FMAs.  Transformed index k: block 0 = k 0..3, 1 = 4..8,
+// 2 = 9..15, 3 = 16..19.
+template <typename T>
+__host__ __device__ __forceinline__ void klein_fwd(const T *r, T *q) {
+  // bubbles E0..E3 (slots 2..5) and fluxes E0..E3 (slots 8..11): orbits of 4
+  {
+    const T s01 = r[2] + r[3], d01 = r[2] - r[3], s23 = r[4] + r[5], d23 = r[4] - r[5];
+    q[10] = s01 + s23; q[0] = s01 - s23; q[17] = d01 + d23; q[4] = d01 - d23;
+  }
+  {
+    const T s01 = r[8] + r[9], d01 = r[8] - r[9], s23 = r[10] + r[11], d23 = r[10] - r[11];
+    q[12] = s01 + s23; q[1] = s01 - s23; q[18] = d01 + d23; q[6] = d01 - d23;
+  }
+  // pressures L(i-1,j), L(i,j-1), U(i-1,j), U(i,j-1) (slots 15, 16, 17, 19)
+  {
+    const T s = r[15] + r[16], d = r[15] - r[16], s2 = r[17] + r[19], d2 = r[17] - r[19];
+    q[3] = s + s2; q[15] = s - s2; q[19] = d + d2; q[8] = d - d2;
+  }
+  // orbits of 2: (ux, uy), bubbles and fluxes on E4, E5, pressures L(i,j), U(i-1,j-1)
+  q[9] = r[0] + r[1]; q[16] = r[0] - r[1];
+  q[11] = r[6] + r[7]; q[5] = r[6] - r[7];
+  q[13] = r[12] + r[13]; q[7] = r[12] - r[13];
+  q[2] = r[14] + r[18]; q[14] = r[14] - r[18];
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void klein_inv(const T *q, T *x) {
+  {
+    const T a = q[10] + q[0], b = q[10] - q[0], c = q[17] + q[4], d = q[17] - q[4];
+    x[2] = a + c; x[3] = a - c; x[4] = b + d; x[5] = b - d;
+  }
+  {
+    const T a = q[12] + q[1], b = q[12] - q[1], c = q[18] + q[6], d = q[18] - q[6];
+    x[8] = a + c; x[9] = a - c; x[10] = b + d; x[11] = b - d;
+  }
+  {
+    const T a = q[3] + q[15], b = q[3] - q[15], c = q[8] + q[19], d = q[8] - q[19];
+    x[15] = a + c; x[16] = a - c; x[17] = b - d; x[19] = b + d;
+  }
+  x[0] = q[9] + q[16]; x[1] = q[9] - q[16];
+  x[6] = q[11] + q[5]; x[7] = q[11] - q[5];
+  x[12] = q[13] + q[7]; x[13] = q[13] - q[7];
+  x[14] = q[2] + q[14]; x[18] = q[2] - q[14];
+}
+
+__host__ __device__ __forceinline__ int klein_block_start(int k) {
+  return k < 4 ? 0 : k < 9 ? 4 : k < 16 ? 9 : 16;
+}
+__host__ __device__ __forceinline__ int klein_block_size(int k) {
+  return k < 4 ? 4 : k < 9 ? 5 : k < 16 ? 7 : 4;
 }
 
 // Packed position of entry (r, c) of a symmetric 20 x 20 matrix (upper triangle, row-major).
@@ -188,6 +253,64 @@ __global__ void __launch_bounds__(64) vanka_setup_kernel(const __grid_constant__
   }
 }
 
+// The shared interior inverse (slot 0) in the symmetry-adapted basis: B = diag(1/d) U^T
+// A^{-1} U diag(1/d), kept only if it is block diagonal and reproduces A^{-1} (relative
+// 1e-9); otherwise the dense slot-0 path stays in use.
+int vanka_klein_setup(Level &L, cudaStream_t st) {
+  L.klein = false;
+  if (!L.uniform || L.psize != 20 || L.n < 2 || L.nslots < 1) return BMG_OK;
+  double packed[210];
+  BMG_CUDA(cudaMemcpy2DAsync(packed, sizeof(double), L.pinv64, sizeof(double) * (size_t)L.nslots,
+                             sizeof(double), 210, cudaMemcpyDeviceToHost, st));
+  BMG_CUDA(cudaStreamSynchronize(st));
+  double Ai[20][20], U[20][20];
+  for (int r = 0; r < 20; ++r)
+    for (int c = 0; c < 20; ++c) Ai[r][c] = packed[sym20(r, c)];
+  for (int s = 0; s < 20; ++s) {          // row s of U = U^T e_s
+    double e[20] = {}, q[20];
+    e[s] = 1.0;
+    klein_fwd(e, q);
+    for (int k = 0; k < 20; ++k) U[s][k] = q[k];
+  }
+  double d[20], B[20][20], amax = 0.0;
+  for (int k = 0; k < 20; ++k) {
+    d[k] = 0.0;
+    for (int s = 0; s < 20; ++s) d[k] += U[s][k] * U[s][k];
+  }
+  for (int r = 0; r < 20; ++r)
+    for (int c = 0; c < 20; ++c) amax = std::fmax(amax, std::fabs(Ai[r][c]));
+  double bmax = 0.0, off = 0.0;
+  for (int k = 0; k < 20; ++k)
+    for (int l = 0; l < 20; ++l) {
+      double acc = 0.0;
+      for (int s = 0; s < 20; ++s)
+        for (int t = 0; t < 20; ++t) acc += U[s][k] * Ai[s][t] * U[t][l];
+      B[k][l] = acc / (d[k] * d[l]);
+      const bool in = klein_block_start(k) == klein_block_start(l);
+      if (in) bmax = std::fmax(bmax, std::fabs(B[k][l]));
+      else off = std::fmax(off, std::fabs(B[k][l]));
+    }
+  if (!(bmax > 0.0) || off > 1e-9 * bmax) return BMG_OK;
+  double err = 0.0;                        // U B U^T against A^{-1}
+  for (int r = 0; r < 20; ++r)
+    for (int c = 0; c < 20; ++c) {
+      double acc = 0.0;
+      for (int k = 0; k < 20; ++k)
+        for (int l = klein_block_start(k); l < klein_block_start(k) + klein_block_size(k); ++l)
+          acc += U[r][k] * B[k][l] * U[c][l];
+      err = std::fmax(err, std::fabs(acc - Ai[r][c]));
+    }
+  if (!(err <= 1e-9 * amax)) return BMG_OK;
+  for (int k = 0; k < 20; ++k)
+    for (int l = 0; l < 7; ++l) {
+      const double v = l < klein_block_size(k) ? B[k][klein_block_start(k) + l] : 0.0;
+      L.kb64[k][l] = v;
+      L.kb32[k][l] = (float)v;
+    }
+  L.klein = true;
+  return BMG_OK;
+}
+
 int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int nrep,
                        double p_shift_area, int psize, int *d_flag, cudaStream_t st) {
   VankaSetupArgs a;
@@ -227,6 +350,8 @@ struct VankaSweepArgs {
   T omega;
   int assign;   // 1: x <- omega M^{-1} r on the free DoFs (x was zero); 0: x += omega M^{-1} r
   const int *gate;
+  int klein;    // slot 0 also given in the symmetry-adapted basis (kb)
+  T kb[20][7];
 };
 
 template <typename T, int kPX, int kPY, int NT>
@@ -281,7 +406,39 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   }
   __syncthreads();
   const size_t ld = (size_t)a.nslots;
-  if (!s_mixed) {
+  if (!s_mixed && a.klein) {
+    // every patch of the tile is an interior patch of uniform coefficients: solve in the
+    // symmetry-adapted basis.  q = U^T r per patch (into sx), x' = B q by (row, patch) tasks
+    // whose row is uniform across a warp (into sr), x = U x' per patch (into sx).
+    for (int p = tid; p < NP; p += NT) {
+      T r[20], q[20];
+#pragma unroll
+      for (int c = 0; c < 20; ++c) r[c] = sr[p * LD + c];
+      klein_fwd(r, q);
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sx[p * LD + c] = q[c];
+    }
+    __syncthreads();
+    for (int t = tid; t < NP * 20; t += NT) {
+      const int k = t / NP, p = t % NP;
+      const int b0 = klein_block_start(k), bs = klein_block_size(k);
+      const T *q = sx + p * LD + b0;
+      T acc = 0;
+#pragma unroll
+      for (int l = 0; l < 7; ++l)
+        if (l < bs) acc = fma(a.kb[k][l], q[l], acc);
+      sr[p * LD + k] = acc;
+    }
+    __syncthreads();
+    for (int p = tid; p < NP; p += NT) {
+      T q[20], x[20];
+#pragma unroll
+      for (int c = 0; c < 20; ++c) q[c] = sr[p * LD + c];
+      klein_inv(q, x);
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
+    }
+  } else if (!s_mixed) {
     // every patch of the tile uses the shared interior inverse (slot 0): thread
     // (row = tid % 20, group = tid / 20) keeps its inverse row in registers and sweeps the
     // group's patches, so the solve issues a few shared loads per patch instead of 400
@@ -399,6 +556,9 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   a.omega = omega;
   a.assign = assign ? 1 : 0;
   a.gate = L.gate;
+  a.klein = L.klein ? 1 : 0;
+  for (int k = 0; k < 20; ++k)
+    for (int l = 0; l < 7; ++l) a.kb[k][l] = sizeof(T) == 8 ? (T)L.kb64[k][l] : (T)L.kb32[k][l];
   BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
   // the largest patch tile that still gives every SM about two CTAs; smaller tiles also
   // spread each patch's rows over more threads
@@ -448,6 +608,8 @@ void make_vanka_args(const Level &L, const double *r, double *x, double omega, b
   a.omega = omega;
   a.assign = assign ? 1 : 0;
   a.gate = gate;
+  a.klein = L.klein ? 1 : 0;
+  std::memcpy(a.kb, L.kb64, sizeof(a.kb));
   std::memcpy(dst, &a, sizeof(a));
 }
 
