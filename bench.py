@@ -302,6 +302,123 @@ def run_batched(args):
         "autotune": not args.no_autotune}))
 
 
+def run_mixed(args):
+    """Mixed-precision workload: the 2048 x 2048 grid, lambda = 1e4, mu = 1, per-triangle
+    lognormal K (sigma = 2, seed 0), right-hand side seed 0; FGMRES(50) to 1e-8 with FP32
+    V-cycles (FP32 accumulation, FP64 patch factors rounded to FP32) against the same solve
+    with FP64 V-cycles.  Reports both times, iterations, the FP64 true residual of both
+    solutions and their relative difference."""
+    import numpy as np
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.mixed_n
+    kL, kU = synthetic.lognormal_k(n, 2.0, 0)
+    K = torch.from_numpy(bmg.pack_k(n, kL, kU)).to(dev)
+    t0 = time.perf_counter()
+    s = bmg.assemble(n, 1e4, 1.0, K, 0.0, 1.0, 1.0, INV_M)
+    h = {p: bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision=p) for p in ("fp32", "fp64")}
+    b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).to(dev)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    x = {p: torch.zeros_like(b) for p in h}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for p in ("fp32", "fp64"):
+        for _ in range(args.warmup):
+            h[p].fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+        ms = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            ev0.record()
+            info = h[p].fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        r = torch.empty_like(b)
+        s.residual(b, x[p], r)
+        out[p] = dict(ms=float(np.median(ms)), iters=info["iters"], status=info["status"],
+                      true_relres=(torch.linalg.norm(r) / torch.linalg.norm(b)).item(),
+                      mdofs=bmg.free_dofs(n) / (float(np.median(ms)) * 1e-3) / 1e6)
+    diff = (torch.linalg.norm(x["fp32"] - x["fp64"]) / torch.linalg.norm(x["fp64"])).item()
+    print(json.dumps({"workload": f"mixed precision {n}x{n}, lambda 1e4, lognormal K sigma 2, "
+                                  "Vanka V(1,1) FGMRES(50) to 1e-8",
+                      "free_dofs": bmg.free_dofs(n), "fp32_mg": out["fp32"], "fp64": out["fp64"],
+                      "speedup_fp32_vs_fp64": out["fp64"]["ms"] / out["fp32"]["ms"],
+                      "rel_diff_fp32_vs_fp64": diff, "setup_s": setup_s,
+                      "steps": args.steps, "warmup": args.warmup}))
+
+
+def run_adjoint(args):
+    """Adjoint workload: J = ||p - p_obs||^2 on the n x n grid (default 1024), p_obs the
+    pressure of the FP64 solve with a reference lognormal log-K field (seed 1), theta the
+    per-triangle log-permeability (FP32, lognormal sigma 1, seed 2), lambda = 10, mu = 1.3;
+    one gradient = forward solve + adjoint solve (MG-FGMRES to 1e-10) + gradient kernel.
+    Checked against central differences of J on --fd-dirs seeded random directions."""
+    import numpy as np
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    from paper_2107_04060_gb300.differentiable import pressure_solve
+    import synthetic
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.adjoint_n
+    cfg = dict(rtol=1e-10, maxit=4000, omega=0.8)
+    lam = torch.tensor(10.0, dtype=torch.float64, device=dev, requires_grad=True)
+    mu = torch.tensor(1.3, dtype=torch.float64, device=dev, requires_grad=True)
+    b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).to(dev)
+    rL, rU = synthetic.lognormal_k(n, 1.0, 1)
+    ref = torch.from_numpy(np.stack([np.log(rL), np.log(rU)]).astype(np.float32)).to(dev)
+    with torch.no_grad():
+        p_obs = pressure_solve(ref, lam.detach(), mu.detach(), b, **cfg)
+    kL, kU = synthetic.lognormal_k(n, 1.0, 2)
+    theta0 = torch.from_numpy(np.stack([np.log(kL), np.log(kU)]).astype(np.float32)).to(dev)
+
+    def J(theta, lam_, mu_):
+        p = pressure_solve(theta, lam_, mu_, b, **cfg)
+        return ((p - p_obs) ** 2).sum()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for it in range(args.warmup + args.steps):
+        theta = theta0.clone().requires_grad_(True)
+        lam.grad = None
+        mu.grad = None
+        torch.cuda.synchronize()
+        ev0.record()
+        loss = J(theta, lam, mu)
+        loss.backward()
+        ev1.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(ev0.elapsed_time(ev1))
+    g = theta.grad.double()
+    Jv = loss.item()
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    errs = []
+    th64 = theta0.double()
+    with torch.no_grad():
+        for _ in range(args.fd_dirs):
+            d = torch.from_numpy(rng.standard_normal((2, n, n))).to(dev)
+            # theta is FP32: perturb in FP64, round, and use the realised step
+            tp, tm = (th64 + h * d).float(), (th64 - h * d).float()
+            jp = J(tp, lam.detach(), mu.detach()).item()
+            jm = J(tm, lam.detach(), mu.detach()).item()
+            fd = (jp - jm) / 2.0
+            an = float((g * (tp.double() - tm.double()) / 2.0).sum().item())
+            errs.append(abs(an - fd) / max(abs(fd), 1e-300))
+    print(json.dumps({"workload": f"adjoint gradient {n}x{n}, J = ||p - p_obs||^2, lambda 10, mu 1.3",
+                      "free_dofs": bmg.free_dofs(n), "ms_per_gradient": float(np.median(times)),
+                      "J": Jv, "dJ_dlambda": lam.grad.item(), "dJ_dmu": mu.grad.item(),
+                      "fd_dirs": args.fd_dirs, "fd_step": h,
+                      "fd_rel_err_max": max(errs) if errs else None,
+                      "fd_rel_err_median": float(np.median(errs)) if errs else None,
+                      "steps": args.steps, "warmup": args.warmup}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,9 +436,13 @@ def main():
     ap.add_argument("--uniform-k", action="store_true", help="--micro: constant K instead of lognormal")
     ap.add_argument("--family", default=None, choices=["apply", "vanka"],
                     help="--micro vcycle: kernel family to time (default vanka)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched"],
-                    help="sweep: the 512^2 parameter sweep (default); batched: the batched "
-                         "workload (--batch-count instances), printed as its own line")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint"],
+                    help="sweep: the 512^2 parameter sweep (default); batched / mixed / adjoint: "
+                         "the batched, 2048^2 mixed-precision and 1024^2 adjoint workloads, each "
+                         "printed as its own line")
+    ap.add_argument("--mixed-n", type=int, default=2048)
+    ap.add_argument("--adjoint-n", type=int, default=1024)
+    ap.add_argument("--fd-dirs", type=int, default=32)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
@@ -340,6 +461,12 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "mixed":
+        run_mixed(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
         return
 
     import numpy as np

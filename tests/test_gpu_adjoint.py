@@ -77,3 +77,44 @@ def test_adjoint_matches_central_differences_32_directions():
         an = float((g * dd).sum())
         worst = max(worst, abs(an - fd) / max(abs(fd), 1e-12 * J.item()))
     assert worst < 1e-4, worst
+
+
+def test_gradient_kernel_full_size_matches_oracle():
+    """The adjoint workload's size (1024 x 1024): given the GPU's forward and adjoint
+    solutions, the gradient kernel agrees with the oracle's element-wise gradient formulas
+    evaluated on the same x and xi: dL/dtheta per triangle to 1e-12 of its maximum;
+    dL/dlambda and dL/dmu are sums of 2M terms of both signs, reduced in a fixed tree of CTA
+    partials on one side and by numpy's pairwise summation on the other, so their difference
+    is bounded by about N eps sum|t_T| (N = 2M, eps = 1.1e-16): 1e-8 relative covers a sum of
+    magnitudes up to 40x the result."""
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    torch.cuda.set_device(0)
+    n = 1024
+    prm = fem.Params(lam=10.0, mu=1.3, tau=1.0, alpha=1.0, inv_M=1.0)
+    kL, kU = synthetic.lognormal_k(n, 1.0, 2)
+    theta = np.stack([np.log(kL), np.log(kU)]).astype(np.float32)
+    P = bmg.pitch(n)
+    th = torch.zeros(2, n + 1, P, dtype=torch.float32, device="cuda")
+    th[:, :n, :n] = torch.from_numpy(theta).cuda()
+    s = bmg.assemble_logk(n, prm.lam, prm.mu, th.reshape(-1), 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.8)
+    b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).cuda()
+    x = torch.zeros_like(b)
+    assert h.fgmres_solve(b, x, rtol=1e-8, maxit=1000)["status"] == "converged"
+    gx = torch.zeros(10, n + 1, P, dtype=torch.float64, device="cuda")
+    gx[8:10, :n, :n] = x.view(10, n + 1, P)[8:10, :n, :n]          # dL/dx for L = ||p||^2 / 2
+    xi = torch.zeros_like(b)
+    assert h.fgmres_solve(gx.reshape(-1), xi, rtol=1e-8, maxit=1000)["status"] == "converged"
+    dth = torch.empty(2 * (n + 1) * P, dtype=torch.float64, device="cuda")
+    dl = torch.empty(2, dtype=torch.float64, device="cuda")
+    s.adjoint_gradient(x, xi, dth, dl)
+    m = Mesh(n)
+    xo = m.pack(bmg.unpack(n, x.cpu().numpy()))
+    xio = m.pack(bmg.unpack(n, xi.cpu().numpy()))
+    th64 = theta.astype(np.float64)
+    do, dlo, dmo = adjoint.gradients(m, prm, th64[0], th64[1], xo, xio)
+    dg = dth.view(2, n + 1, P)[:, :n, :n].cpu().numpy()
+    assert np.abs(dg - do).max() <= 1e-12 * np.abs(do).max()
+    assert dl[0].item() == pytest.approx(dlo, rel=1e-8)
+    assert dl[1].item() == pytest.approx(dmo, rel=1e-8)
