@@ -170,7 +170,10 @@ typedef struct {
 /*
  * bmg_fgmres_solve -- x ~= A^{-1} b by right-preconditioned flexible GMRES(m) with one
  * V-cycle of h as the preconditioner (Sec. 5.1).  Arnoldi by classical Gram-Schmidt with
- * one re-orthogonalisation pass, all in FP64.  b, x: device vectors.  The call returns
+ * one re-orthogonalisation pass: the first pass's coefficients come from an FP32 copy of
+ * the basis, the second pass and every vector update are FP64 (the Hessenberg column is the
+ * sum of both passes, so it and the basis are FP64-accurate).  b, x: device vectors.  The
+ * call returns
  * after the solve has finished (it synchronises `stream` once per iteration to read the
  * Hessenberg column).  info may be NULL.
  */
@@ -218,8 +221,10 @@ long long bmg_launch_count(void);
 int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
 /*
- * bmg_fgmres_solve_noalloc -- the same solve as bmg_fgmres_solve (same algorithm, kernels
- * and results) for callers that cannot allocate device memory while they run: code that
+ * bmg_fgmres_solve_noalloc -- the FGMRES solve of bmg_fgmres_solve (same V-cycle, same
+ * CGS2 Arnoldi, except that its first Gram-Schmidt pass runs in FP64 where bmg_fgmres_solve
+ * takes it from an FP32 copy of the basis: iteration counts agree within one and both meet
+ * the tolerance) for callers that cannot allocate device memory while they run: code that
  * works inside a fixed memory budget or a framework that owns every device allocation, or
  * that calls in from a context where cudaMalloc is not allowed.  bmg_fgmres_solve allocates
  * its Krylov workspace with cudaMalloc on its first call (and again when `restart` grows);

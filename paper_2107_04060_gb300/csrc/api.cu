@@ -530,6 +530,7 @@ extern "C" void bmg_destroy_hierarchy(bmg_hierarchy *h) {
   for (auto &L : h->levels) free_level(L);
   cudaFree(h->d_flag);
   cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r); cudaFree(h->xb);
+  cudaFree(h->V32);
   cudaFree(h->partial); cudaFree(h->dres);
   cudaFreeHost(h->hres);
   cudaFree(h->hostbuf_b); cudaFree(h->hostbuf_x);
@@ -600,12 +601,14 @@ static const int kDotBlocks = 152 * 4;
 
 static int ensure_krylov(bmg_hierarchy *h, int m) {
   if (h->m_alloc >= m) return BMG_OK;
-  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r);
+  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r); cudaFree(h->V32);
   cudaFree(h->partial); cudaFree(h->dres); cudaFreeHost(h->hres);
   h->V = h->Z = h->w = h->r = h->partial = h->dres = h->hres = nullptr;
+  h->V32 = nullptr;
   h->m_alloc = 0;
   const size_t vl = vec_len_of(h->sys->n);
   BMG_CUDA(cudaMalloc(&h->V, sizeof(double) * vl * (m + 1)));
+  BMG_CUDA(cudaMalloc(&h->V32, sizeof(float) * vl * (m + 1)));
   BMG_CUDA(cudaMalloc(&h->Z, sizeof(double) * vl * m));
   BMG_CUDA(cudaMalloc(&h->w, sizeof(double) * vl));
   BMG_CUDA(cudaMalloc(&h->r, sizeof(double) * vl));
@@ -671,7 +674,7 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &beta, sizeof(double), cudaMemcpyHostToDevice, st));
-    if ((rc = launch_scale(h->r, h->V, h->dres + 3 * (m + 2), vl, st))) return rc;
+    if ((rc = launch_scale2(h->r, h->V, h->V32, h->dres + 3 * (m + 2), vl, st))) return rc;
     int k = 0;
     bool stop = false;
     for (int j = 0; j < m && !stop; ++j) {
@@ -680,8 +683,9 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if ((rc = vcycle_any(h, vj, zj, st))) return rc;
       if ((rc = launch_apply<double>(h->fine_op, zj, nullptr, h->w, false, 1, 0, st))) return rc;
       double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
-      // CGS2: h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with ||w||^2
-      if ((rc = launch_dots(h->V, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d1, st))) return rc;
+      // CGS2: h1 = V^T w (from the FP32 copy of V); w -= V h1 fused with h2 = V^T w;
+      // w -= V h2 fused with ||w||^2
+      if ((rc = launch_dots32(h->V32, ldv, j + 1, h->w, vl, h->partial, kDotBlocks, d1, st))) return rc;
       if ((rc = launch_update_dots(h->w, h->V, ldv, j + 1, d1, vl, 1, h->partial, kDotBlocks, d2, st))) return rc;
       if ((rc = launch_update_dots(h->w, h->V, ldv, j + 1, d2, vl, 0, h->partial, kDotBlocks, d3, st))) return rc;
       BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
@@ -697,7 +701,8 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if (!finite) { inf.status = BMG_DIVERGED; stop = true; k = j; break; }
       if (hn > 0.0) {
         BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &Hij(j + 1, j), sizeof(double), cudaMemcpyHostToDevice, st));
-        if ((rc = launch_scale(h->w, h->V + (size_t)(j + 1) * ldv, h->dres + 3 * (m + 2), vl, st))) return rc;
+        if ((rc = launch_scale2(h->w, h->V + (size_t)(j + 1) * ldv, h->V32 + (size_t)(j + 1) * ldv,
+                                h->dres + 3 * (m + 2), vl, st))) return rc;
       }
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);

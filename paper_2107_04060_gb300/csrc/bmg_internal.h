@@ -216,6 +216,7 @@ struct bmg_hierarchy {
   // FGMRES workspace (FP64)
   int m_alloc = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *xb = nullptr;
+  float *V32 = nullptr;        // FP32 copy of the basis (first Gram-Schmidt pass)
   double *partial = nullptr;   // [kMaxDot][nblocks]
   double *dres = nullptr;      // device results of reductions
   double *hres = nullptr;      // pinned host mirror
@@ -289,6 +290,9 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
 int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                        int dots, double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st);
+int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st);
+int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
+                  int nblocks, double *out, cudaStream_t st);
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y,
                       size_t n, cudaStream_t st);
 }  // namespace bmg

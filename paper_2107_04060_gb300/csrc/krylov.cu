@@ -117,6 +117,61 @@ int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n, d
   return BMG_OK;
 }
 
+// First Gram-Schmidt pass from an FP32 copy of the basis: partial[q * nblocks + b] = sum
+// over block b's chunk of V32_q . w (q < k), products and the per-thread sums in FP32 (a
+// thread covers a few dozen elements), the CTA and grid sums in FP64.  The pass only has to
+// remove most of w's component along the basis: the FP64 second pass that follows measures
+// and removes what it left (to FP64 accuracy), and the Hessenberg column is the sum of the
+// two passes' coefficients.
+__global__ void __launch_bounds__(256) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
+                                                     const double *__restrict__ w, size_t n,
+                                                     double *__restrict__ partial) {
+  constexpr int G = 8;
+  __shared__ double red[G][8];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t c0 = blockIdx.x * chunk;
+  const size_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q0 = 0; q0 < k; q0 += G) {
+    const int cnt = (k - q0) < G ? (k - q0) : G;
+    float acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = 0.f;
+    for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      const float wi = (float)w[i];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < cnt) acc[g] = fmaf(V[(size_t)(q0 + g) * ldv + i], wi, acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      double a = (double)acc[g];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
+      if (lane == 0) red[g][wid] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
+      for (int u = 0; u < 8; ++u) t += red[threadIdx.x][u];
+      partial[(size_t)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// out[0..k-1] = V32_q . w (first Gram-Schmidt pass, see dots32_kernel)
+int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
+                  int nblocks, double *out, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
+  dots32_kernel<<<nblocks, 256, 0, st>>>(V, ldv, k, w, n, partial);
+  BMG_CHECK_LAUNCH("dots32_kernel");
+  reduce_partials_kernel<<<k, 256, 0, st>>>(partial, nblocks, k, out);
+  BMG_PROF_END(st, 0.0);
+  BMG_CHECK_LAUNCH("reduce_partials_kernel");
+  return BMG_OK;
+}
+
 // w -= sum_q h[q] V_q
 __global__ void update_kernel(double *__restrict__ w, const double *__restrict__ V, size_t ldv,
                               int k, const double *__restrict__ h, size_t n) {
@@ -211,6 +266,24 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = w[i] * d;
 }
+// v = w / s[0] and its FP32 copy v32
+__global__ void scale2_kernel(const double *__restrict__ w, double *__restrict__ v, float *__restrict__ v32,
+                              const double *__restrict__ s, size_t n) {
+  const double d = s[0] != 0.0 ? 1.0 / s[0] : 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double x = w[i] * d;
+    v[i] = x;
+    v32[i] = (float)x;
+  }
+}
+int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
+  scale2_kernel<<<152 * 8, 256, 0, st>>>(w, v, v32, s, n);
+  BMG_PROF_END(st, 0.0);
+  BMG_CHECK_LAUNCH("scale2_kernel");
+  return BMG_OK;
+}
+
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   scale_kernel<<<152 * 8, 256, 0, st>>>(w, v, s, n);
