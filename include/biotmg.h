@@ -260,7 +260,8 @@ size_t bmg_noalloc_capacity(void);
  *   o: rtol, restart, maxit and x0_is_zero for every instance (as for bmg_fgmres_solve).
  *   autotune != 0: time every candidate tile of the batched operator and Vanka kernels on
  *     this batch (per level size) and keep the fastest; 0: the single-instance rule.
- *   Allocates the Krylov workspace of every instance ((2m + 5) vectors of its size) and
+ *   Allocates the Krylov workspace of every instance ((2m + 5) FP64 vectors of its size and
+ *   an FP32 copy of its m + 1 basis vectors) and
  *   records the solve as one CUDA graph: a prologue (copy-in, ||b||), a device-side while
  *   loop whose body closes cycles and takes one Arnoldi step for every open instance, and
  *   an epilogue (copy-out).  Returns BMG_ERR_ARG on an invalid batch (message names why).

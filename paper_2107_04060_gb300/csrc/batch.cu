@@ -48,6 +48,7 @@ struct BInst {
   size_t vl;
   int nb, item0;      // vector items of this instance: item0 .. item0 + nb - 1
   double *B, *X, *R, *W, *V, *Z, *Q, *Zc;
+  float *V32;         // FP32 copy of the basis (first Gram-Schmidt pass)
   double *partial;    // [(m + 2)][nb]
   double *d;          // [3][m + 2]: reduced products of the three Arnoldi passes
   double *H;          // [(m + 1)][m]
@@ -88,7 +89,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_copyout_kernel(const BInst 
 
 // Block-partial products of one Arnoldi pass (or a norm), with the preceding update:
 //   OP_NORM_B: b.b                       OP_NORM_R: r.r (gate_end)
-//   OP_CGS1:   V_q.w (q <= j), w.w; also Z_j = z (gate_iter)
+//   OP_CGS1:   V_q.w (q <= j) from the FP32 copy of V (FP32 products and per-thread sums,
+//              FP64 beyond); also Z_j = z (gate_iter)
 //   OP_CGS2:   w -= V d1; V_q.w (q <= j), w.w
 //   OP_CGS3:   w -= V d2; w.w
 // Products are stored at partial[slot][chunk] (slot q for V_q.w, slot j + 1 for w.w; slot 0
@@ -112,8 +114,39 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
   const double *h = op == OP_CGS2 ? a.d : a.d + (m + 2);
   double *w = op == OP_NORM_B ? a.B : op == OP_NORM_R ? a.R : a.W;
   double *zj = a.Z + (size_t)s.j * vl;
-  const int nd = vdots ? k + 1 : 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (op == OP_CGS1) {
+    const float *V32 = a.V32;
+    for (int q0 = 0; q0 < k; q0 += G) {
+      const int cnt = min(G, k - q0);
+      float acc[G];
+#pragma unroll
+      for (int gi = 0; gi < G; ++gi) acc[gi] = 0.f;
+      for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
+        const float wi = (float)w[i];
+        if (q0 == 0) zj[i] = a.Zc[i];
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi)
+          if (gi < cnt) acc[gi] = fmaf(V32[(size_t)(q0 + gi) * vl + i], wi, acc[gi]);
+      }
+#pragma unroll
+      for (int gi = 0; gi < G; ++gi) {
+        double t = (double)acc[gi];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
+        if (lane == 0) red[gi][wid] = t;
+      }
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        double t = 0.0;
+        for (int u = 0; u < kVecThreads / 32; ++u) t += red[threadIdx.x][u];
+        a.partial[(size_t)(q0 + threadIdx.x) * a.nb + chunk] = t;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  const int nd = vdots ? k + 1 : 1;
   for (int q0 = 0; q0 < nd; q0 += G) {
     const int cnt = min(G, nd - q0);
     double acc[G];
@@ -126,7 +159,6 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
           for (int p = 0; p < k; ++p) wi = fma(-h[p], a.V[(size_t)p * vl + i], wi);
           w[i] = wi;
         }
-        if (op == OP_CGS1) zj[i] = a.Zc[i];
       }
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
@@ -159,7 +191,7 @@ __global__ void __launch_bounds__(128) batch_reduce_kernel(const BInst *__restri
   const BInst &a = I[blockIdx.y];
   const BState &s = *a.s;
   if (op == OP_NORM_R ? !s.gate_end : (op >= OP_CGS1 && !s.gate_iter)) return;
-  const int nd = (op == OP_CGS1 || op == OP_CGS2) ? s.j + 2 : 1;
+  const int nd = op == OP_CGS1 ? s.j + 1 : op == OP_CGS2 ? s.j + 2 : 1;
   const int slot = blockIdx.x;
   if (slot >= nd) return;
   __shared__ double red[128];
@@ -204,11 +236,13 @@ __global__ void __launch_bounds__(kVecThreads) batch_basis_kernel(const BInst *_
   const double den = s.fresh ? s.beta : s.hnext;
   const double dinv = den != 0.0 ? 1.0 / den : 0.0;
   double *vj = a.V + (size_t)s.j * a.vl;
+  float *vj32 = a.V32 + (size_t)s.j * a.vl;
   const size_t c0 = (size_t)(blockIdx.x - a.item0) * kChunk;
   const size_t c1 = min(a.vl, c0 + kChunk);
   for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
     const double v = src[i] * dinv;
     vj[i] = v;
+    vj32[i] = (float)v;
     a.Q[i] = v;
   }
 }
@@ -383,6 +417,7 @@ struct bmg_batch {
   double **d_user = nullptr;            // [2][count]: b pointers, then x pointers
   unsigned char *d_args = nullptr;      // arguments of the batched level launches
   std::vector<double *> bufs;           // per-instance allocations
+  std::vector<float *> fbufs;
   std::vector<unsigned char *> masks;   // coarsest-level free masks
   // host staging (pinned)
   double **h_user = nullptr;
@@ -598,6 +633,7 @@ extern "C" void bmg_batch_destroy(bmg_batch *bt) {
   if (bt->graph) cudaGraphDestroy(bt->graph);
   if (bt->cap) cudaStreamDestroy(bt->cap);
   for (double *p : bt->bufs) cudaFree(p);
+  for (float *p : bt->fbufs) cudaFree(p);
   for (unsigned char *p : bt->masks) cudaFree(p);
   cudaFree(bt->d_inst);
   cudaFree(bt->d_state);
@@ -684,6 +720,9 @@ extern "C" int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_k
         (rc = dalloc(&a.cs, m + 1)) || (rc = dalloc(&a.sn, m + 1)) || (rc = dalloc(&a.g, m + 1)) ||
         (rc = dalloc(&a.y, m + 1)))
       return fail(rc);
+    if (cudaMalloc(&a.V32, sizeof(float) * a.vl * (m + 1)) != cudaSuccess)
+      return fail(cuda_fail(cudaErrorMemoryAllocation, "batch buffers"));
+    bt->fbufs.push_back(a.V32);
     a.Q = (double *)L0.rhs;
     a.Zc = (double *)L0.z;
     a.s = bt->d_state + q;
