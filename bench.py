@@ -448,6 +448,8 @@ def main():
     ap.add_argument("--no-sequential", action="store_true")
     ap.add_argument("--breakdown", action="store_true",
                     help="print the device time per kernel family of one step and exit")
+    ap.add_argument("--breakdown-levels", action="store_true",
+                    help="with --breakdown: also per grid level (one step per family and level)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -570,10 +572,21 @@ def main():
             one_step("fp64")
             torch.cuda.synchronize()
             out[fam] = bmg.profile_stop()
+        levels = {}
+        if args.breakdown_levels:
+            m = n
+            while m >= 16:
+                for fam in ("apply", "vanka", "vanka_u", "restrict", "prolong"):
+                    bmg.profile_start(fam, m)
+                    one_step("fp64")
+                    torch.cuda.synchronize()
+                    r = bmg.profile_stop()
+                    levels.setdefault(str(m), {})[fam] = [round(r["ms"], 3), r["launches"]]
+                m //= 2
         ms_step, _, _, _ = timed("fp64", 1)
         print(json.dumps({"breakdown_ms": {k: round(v["ms"], 3) for k, v in out.items()},
                           "launches": {k: v["launches"] for k, v in out.items()},
-                          "step_ms": ms_step}))
+                          "per_level_ms_launches": levels, "step_ms": ms_step}))
         return
 
     # ---- timed region (FP64 V-cycle), clocks sampled meanwhile

@@ -153,6 +153,32 @@ struct Level {
 // matrix V A V^T of the symmetric A) and kept as its upper triangle; the 8 x 8 one is full.
 inline int patch_entries(int psize) { return psize == 20 ? 210 : psize * psize; }
 
+// ---- programmatic dependent launch ------------------------------------------------------
+// The kernels of the solve path are launched with programmatic stream serialisation and
+// start with pdl_enter(): it waits until the grids they depend on have completed and their
+// writes are visible (a no-op for a launch without a programmatic dependency), then lets the
+// next kernel of the stream start launching, so its launch overlaps this kernel's last wave.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Kernel prologue: leave when a gate is present and closed.
 #define BMG_GATE(g) if ((g) != nullptr && *(g) == 0) return
 

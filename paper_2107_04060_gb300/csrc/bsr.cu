@@ -131,6 +131,7 @@ struct VankaUArgs {
 // as the 20-DoF sweep: residual gather, (patch, row) solve tasks, weighted gather.
 template <typename T, int kQX, int kQY, int NT>
 __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ VankaUArgs<T> a) {
+  pdl_enter();
   BMG_GATE(a.gate);
   constexpr int NP = kQX * kQY, LD = 9;
   __shared__ T sr[NP * LD];
@@ -232,6 +233,7 @@ struct DpArgs {
 
 template <typename T>
 __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
+  pdl_enter();
   BMG_GATE(a.gate);
   const int ci = blockIdx.x * blockDim.x + threadIdx.x;
   const int cj = blockIdx.y * blockDim.y + threadIdx.y;
@@ -286,6 +288,7 @@ struct RyArgs {
 
 template <typename T>
 __global__ void bsr_ry_kernel(const __grid_constant__ RyArgs<T> a) {
+  pdl_enter();
   BMG_GATE(a.gate);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -327,7 +330,7 @@ __global__ void bsr_ry_kernel(const __grid_constant__ RyArgs<T> a) {
 template <typename T, int QX, int QY, int NT>
 static void launch_vanka_u_tile(const VankaUArgs<T> &a, const Level &L, cudaStream_t st) {
   dim3 grid((L.g.pitch + QX - 2) / (QX - 1), (L.n + 1 + QY - 2) / (QY - 1));
-  vanka_u_kernel<T, QX, QY, NT><<<grid, NT, 0, st>>>(a);
+  (void)launch_pdl(vanka_u_kernel<T, QX, QY, NT>, dim3(grid), dim3(NT), 0, st, a);
 }
 
 template <typename T>
@@ -391,7 +394,7 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
   dim3 b(32, 8), gr((L.n + 31) / 32, (L.n + 7) / 8);
   { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
-  bsr_dp_kernel<T><<<gr, b, 0, st>>>(a);
+  BMG_CUDA(launch_pdl(bsr_dp_kernel<T>, dim3(gr), dim3(b), 0, st, a));
     BMG_PROF_END(st, 0.0); }
   BMG_CHECK_LAUNCH("bsr_dp_kernel");
   // r_y - B^T dp on the u and w blocks
@@ -407,7 +410,7 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   }
   dim3 rb(32, 8), rg((L.g.pitch + 31) / 32, (L.n + 1 + 7) / 8);
   { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
-  bsr_ry_kernel<T><<<rg, rb, 0, st>>>(ra);
+  BMG_CUDA(launch_pdl(bsr_ry_kernel<T>, dim3(rg), dim3(rb), 0, st, ra));
     BMG_PROF_END(st, 0.0); }
   BMG_CHECK_LAUNCH("bsr_ry_kernel");
   return launch_vanka_u<T>(L, ry, nullptr, x, d, omega, 1, assign, st);

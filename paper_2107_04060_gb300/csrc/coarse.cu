@@ -152,6 +152,7 @@ template <typename T>
 __global__ void coarse_solve_kernel(const T *__restrict__ inv, const int *__restrict__ free_idx,
                                     int N, const T *__restrict__ r, T *__restrict__ z,
                                     const int *gate) {
+  pdl_enter();
   BMG_GATE(gate);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -172,7 +173,7 @@ int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (L.nfree * 32 + threads - 1) / threads;
   { BMG_PROF_BEGIN(BMG_PROF_COARSE, 0, st);
-  coarse_solve_kernel<T><<<blocks, threads, 0, st>>>(inv, L.free_idx, L.nfree, r, z, L.gate);
+  BMG_CUDA(launch_pdl(coarse_solve_kernel<T>, dim3(blocks), dim3(threads), 0, st, inv, L.free_idx, L.nfree, r, z, L.gate));
     BMG_PROF_END(st, (double)L.n * L.n); }
   BMG_CHECK_LAUNCH("coarse_solve_kernel");
   return BMG_OK;

@@ -7,6 +7,7 @@ namespace bmg {
 
 template <typename T>
 __global__ void fill_kernel(T *x, T v, size_t n, const int *gate) {
+  pdl_enter();
   BMG_GATE(gate);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     x[i] = v;
@@ -17,7 +18,7 @@ int launch_fill(T *x, T v, size_t n, cudaStream_t st, const int *gate) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  fill_kernel<T><<<blocks, 256, 0, st>>>(x, v, n, gate);
+  BMG_CUDA(launch_pdl(fill_kernel<T>, dim3(blocks), dim3(256), 0, st, x, v, n, gate));
   BMG_CHECK_LAUNCH("fill_kernel");
   return BMG_OK;
 }
@@ -25,20 +26,22 @@ template int launch_fill<double>(double *, double, size_t, cudaStream_t, const i
 template int launch_fill<float>(float *, float, size_t, cudaStream_t, const int *);
 
 __global__ void d2f_kernel(const double *x, float *y, size_t n) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
 __global__ void f2d_kernel(const float *x, double *y, size_t n) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
 }
 int launch_convert_d2f(const double *x, float *y, size_t n, cudaStream_t st) {
-  d2f_kernel<<<152 * 8, 256, 0, st>>>(x, y, n);
+  BMG_CUDA(launch_pdl(d2f_kernel, dim3(152 * 8), dim3(256), 0, st, x, y, n));
   BMG_CHECK_LAUNCH("d2f_kernel");
   return BMG_OK;
 }
 int launch_convert_f2d(const float *x, double *y, size_t n, cudaStream_t st) {
-  f2d_kernel<<<152 * 8, 256, 0, st>>>(x, y, n);
+  BMG_CUDA(launch_pdl(f2d_kernel, dim3(152 * 8), dim3(256), 0, st, x, y, n));
   BMG_CHECK_LAUNCH("f2d_kernel");
   return BMG_OK;
 }
@@ -50,6 +53,7 @@ int launch_convert_f2d(const float *x, double *y, size_t n, cudaStream_t st) {
 __global__ void __launch_bounds__(256) dots_kernel(const double *__restrict__ V, size_t ldv, int k,
                                                    const double *__restrict__ w, size_t n,
                                                    double *__restrict__ partial) {
+  pdl_enter();
   constexpr int G = 8;
   __shared__ double red[G][8];
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -91,6 +95,7 @@ __global__ void __launch_bounds__(256) dots_kernel(const double *__restrict__ V,
 
 __global__ void reduce_partials_kernel(const double *__restrict__ partial, int nblocks, int cnt,
                                        double *__restrict__ out) {
+  pdl_enter();
   const int q = blockIdx.x;
   if (q >= cnt) return;
   __shared__ double red[256];
@@ -109,9 +114,9 @@ __global__ void reduce_partials_kernel(const double *__restrict__ partial, int n
 int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                 int nblocks, double *out, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  dots_kernel<<<nblocks, 256, 0, st>>>(V, ldv, k, w, n, partial);
+  BMG_CUDA(launch_pdl(dots_kernel, dim3(nblocks), dim3(256), 0, st, V, ldv, k, w, n, partial));
   BMG_CHECK_LAUNCH("dots_kernel");
-  reduce_partials_kernel<<<k + 1, 256, 0, st>>>(partial, nblocks, k + 1, out);
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k + 1), dim3(256), 0, st, partial, nblocks, k + 1, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
@@ -126,6 +131,7 @@ int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n, d
 __global__ void __launch_bounds__(256) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
                                                      const double *__restrict__ w, size_t n,
                                                      double *__restrict__ partial) {
+  pdl_enter();
   constexpr int G = 8;
   __shared__ double red[G][8];
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -164,9 +170,9 @@ __global__ void __launch_bounds__(256) dots32_kernel(const float *__restrict__ V
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                   int nblocks, double *out, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  dots32_kernel<<<nblocks, 256, 0, st>>>(V, ldv, k, w, n, partial);
+  BMG_CUDA(launch_pdl(dots32_kernel, dim3(nblocks), dim3(256), 0, st, V, ldv, k, w, n, partial));
   BMG_CHECK_LAUNCH("dots32_kernel");
-  reduce_partials_kernel<<<k, 256, 0, st>>>(partial, nblocks, k, out);
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, partial, nblocks, k, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
@@ -175,6 +181,7 @@ int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, 
 // w -= sum_q h[q] V_q
 __global__ void update_kernel(double *__restrict__ w, const double *__restrict__ V, size_t ldv,
                               int k, const double *__restrict__ h, size_t n) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double acc = w[i];
     for (int q = 0; q < k; ++q) acc = fma(-h[q], V[(size_t)q * ldv + i], acc);
@@ -184,7 +191,7 @@ __global__ void update_kernel(double *__restrict__ w, const double *__restrict__
 int launch_update(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                   cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  update_kernel<<<152 * 8, 256, 0, st>>>(w, V, ldv, k, h, n);
+  BMG_CUDA(launch_pdl(update_kernel, dim3(152 * 8), dim3(256), 0, st, w, V, ldv, k, h, n));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("update_kernel");
   return BMG_OK;
@@ -198,6 +205,7 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
 __global__ void __launch_bounds__(256) update_dots_kernel(double *__restrict__ w, const double *__restrict__ V,
                                                           size_t ldv, int k, const double *__restrict__ h,
                                                           size_t n, int dots, double *__restrict__ partial) {
+  pdl_enter();
   constexpr int G = 8;
   __shared__ double red[G][8];
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -250,10 +258,10 @@ __global__ void __launch_bounds__(256) update_dots_kernel(double *__restrict__ w
 int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                        int dots, double *partial, int nblocks, double *out, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  update_dots_kernel<<<nblocks, 256, 0, st>>>(w, V, ldv, k, h, n, dots, partial);
+  BMG_CUDA(launch_pdl(update_dots_kernel, dim3(nblocks), dim3(256), 0, st, w, V, ldv, k, h, n, dots, partial));
   BMG_CHECK_LAUNCH("update_dots_kernel");
   const int cnt = dots ? k + 1 : 1;
-  reduce_partials_kernel<<<cnt, 256, 0, st>>>(partial, nblocks, cnt, out);
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(cnt), dim3(256), 0, st, partial, nblocks, cnt, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
@@ -262,6 +270,7 @@ int launch_update_dots(double *w, const double *V, size_t ldv, int k, const doub
 // v = w / s[0]   (s on the device; s[0] == 0 leaves v = 0)
 __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ v,
                              const double *__restrict__ s, size_t n) {
+  pdl_enter();
   const double d = s[0] != 0.0 ? 1.0 / s[0] : 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = w[i] * d;
@@ -269,6 +278,7 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
 // v = w / s[0] and its FP32 copy v32
 __global__ void scale2_kernel(const double *__restrict__ w, double *__restrict__ v, float *__restrict__ v32,
                               const double *__restrict__ s, size_t n) {
+  pdl_enter();
   const double d = s[0] != 0.0 ? 1.0 / s[0] : 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double x = w[i] * d;
@@ -278,7 +288,7 @@ __global__ void scale2_kernel(const double *__restrict__ w, double *__restrict__
 }
 int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  scale2_kernel<<<152 * 8, 256, 0, st>>>(w, v, v32, s, n);
+  BMG_CUDA(launch_pdl(scale2_kernel, dim3(152 * 8), dim3(256), 0, st, w, v, v32, s, n));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("scale2_kernel");
   return BMG_OK;
@@ -286,7 +296,7 @@ int launch_scale2(const double *w, double *v, float *v32, const double *s, size_
 
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  scale_kernel<<<152 * 8, 256, 0, st>>>(w, v, s, n);
+  BMG_CUDA(launch_pdl(scale_kernel, dim3(152 * 8), dim3(256), 0, st, w, v, s, n));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("scale_kernel");
   return BMG_OK;
@@ -295,6 +305,7 @@ int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStre
 // x += sum_q y[q] Z_q
 __global__ void axpy_multi_kernel(double *__restrict__ x, const double *__restrict__ Z, size_t ldz,
                                   int k, const double *__restrict__ y, size_t n) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double acc = x[i];
     for (int q = 0; q < k; ++q) acc = fma(y[q], Z[(size_t)q * ldz + i], acc);
@@ -304,7 +315,7 @@ __global__ void axpy_multi_kernel(double *__restrict__ x, const double *__restri
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y, size_t n,
                       cudaStream_t st) {
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  axpy_multi_kernel<<<152 * 8, 256, 0, st>>>(x, Z, ldz, k, y, n);
+  BMG_CUDA(launch_pdl(axpy_multi_kernel, dim3(152 * 8), dim3(256), 0, st, x, Z, ldz, k, y, n));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("axpy_multi_kernel");
   return BMG_OK;

@@ -193,6 +193,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, int bx, int by
 
 template <typename T, int WM, int kTX, int kTY, int NT>
 __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+  pdl_enter();
   BMG_GATE(a.gate);
   apply_tile<T, WM, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, (size_t)blockIdx.z * a.bstride);
 }
@@ -222,7 +223,7 @@ static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, c
       attr = true;
     }
   }
-  apply_kernel<T, WM, TX, TY, NT><<<grid, block, smem, st>>>(a);
+  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT>, dim3(grid), dim3(block), smem, st, a));
   return BMG_OK;
 }
 

@@ -31,6 +31,7 @@ int upload_transfer_tables() {
 template <typename T>
 __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc,
                                 const int *gate) {
+  pdl_enter();
   BMG_GATE(gate);
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -59,6 +60,7 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
 template <typename T>
 __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf,
                                const int *gate) {
+  pdl_enter();
   BMG_GATE(gate);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -87,7 +89,7 @@ int launch_restrict(const Level &fine, const Level &coarse, const T *rf, T *rc, 
   dim3 block(32, 4);
   dim3 grid((coarse.g.pitch + 31) / 32, (coarse.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_RESTRICT, fine.n, st);
-  restrict_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, rf, rc, fine.gate);
+  BMG_CUDA(launch_pdl(restrict_kernel<T>, dim3(grid), dim3(block), 0, st, fine.g, coarse.g, rf, rc, fine.gate));
     BMG_PROF_END(st, (double)fine.n * fine.n); }
   BMG_CHECK_LAUNCH("restrict_kernel");
   return BMG_OK;
@@ -99,7 +101,7 @@ int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *x
   dim3 block(32, 4);
   dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_PROLONG, fine.n, st);
-  prolong_kernel<T><<<grid, block, 0, st>>>(fine.g, coarse.g, xc, xf, fine.gate);
+  BMG_CUDA(launch_pdl(prolong_kernel<T>, dim3(grid), dim3(block), 0, st, fine.g, coarse.g, xc, xf, fine.gate));
     BMG_PROF_END(st, (double)fine.n * fine.n); }
   BMG_CHECK_LAUNCH("prolong_kernel");
   return BMG_OK;

@@ -520,6 +520,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
 
 template <typename T, int kPX, int kPY, int NT>
 __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+  pdl_enter();
   BMG_GATE(a.gate);
   vanka_tile<T, kPX, kPY, NT>(a, blockIdx.x, blockIdx.y);
 }
@@ -537,7 +538,7 @@ template <typename T, int PX, int PY, int NT>
 static void launch_vanka_tile(const VankaSweepArgs<T> &a, const Level &L, cudaStream_t st) {
   static_assert(2 * PX * PY * 21 * sizeof(T) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
   dim3 grid((L.g.pitch + PX - 2) / (PX - 1), (L.n + 1 + PY - 2) / (PY - 1));
-  vanka_sweep_kernel<T, PX, PY, NT><<<grid, NT, 0, st>>>(a);
+  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT>, dim3(grid), dim3(NT), 0, st, a);
 }
 
 static long long vanka_ctas(const Level &L, int px, int py) {
