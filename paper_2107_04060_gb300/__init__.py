@@ -67,6 +67,7 @@ _sig = {
     "bmg_noalloc_capacity": (C.c_size_t, []),
     "bmg_system_n": (C.c_int, [_vp]),
     "bmg_hierarchy_levels": (C.c_int, [_vp]),
+    "bmg_hierarchy_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
     "bmg_destroy_system": (None, [_vp]),
     "bmg_destroy_hierarchy": (None, [_vp]),
     "bmg_status_string": (C.c_char_p, [C.c_int]),
@@ -236,6 +237,10 @@ class Hierarchy:
 
     def vcycle(self, r, z, stream=None):
         _check(lib.bmg_vcycle(self._h, _ptr(r), _ptr(z), _stream(stream)), "bmg_vcycle")
+
+    def tile(self, level: int, kernel: str) -> int:
+        """Tile index chosen at setup for a kernel family on a level (``bmg_hierarchy_tile``)."""
+        return lib.bmg_hierarchy_tile(self._h, level, PROF[kernel])
 
     def fgmres_solve(self, b, x, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True, stream=None):
         ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)

@@ -2,6 +2,7 @@
 // Host code only orchestrates: every arithmetic step of assembly, relaxation, transfer,
 // coarse solve and Krylov iteration runs in this library's kernels.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -81,6 +82,7 @@ static int alloc_coefs(Level &L, bool full) {
 }
 
 static void free_level(Level &L) {
+  free_apply_tma(L);
   if (L.owns_coefs) {
     cudaFree(L.kinv64); cudaFree(L.kinv32); cudaFree(L.wm64); cudaFree(L.wm32);
   }
@@ -375,9 +377,17 @@ template <typename T>
 static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
   T *z = (T *)L.z, *t = (T *)L.t;
   const T *r = (const T *)L.rhs;
-  int rc = pick_tile(&L.tile_apply, 0, 4, [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); },
-                     e0, e1, st);
-  if (rc) return rc;
+  // candidates 0-4: tile shapes; 5 (FP32): 32 x 8 with the input staged by TMA.  The
+  // environment variable BMG_FORCE_APPLY_TILE fixes the choice (testing the variants).
+  int rc;
+  const char *force = std::getenv("BMG_FORCE_APPLY_TILE");
+  if (force && *force) {
+    L.tile_apply = std::atoi(force);
+  } else {
+    rc = pick_tile(&L.tile_apply, 0, sizeof(T) == 4 ? 5 : 4,
+                   [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); }, e0, e1, st);
+    if (rc) return rc;
+  }
   if (h->opts.smoother == BMG_VANKA)
     return pick_tile(&L.tile_vanka, sizeof(T) == 4 ? 0 : 1, 4,
                      [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
@@ -481,6 +491,13 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
     cudaMemsetAsync(L.z, 0, es * vl, st);
     cudaMemsetAsync(L.t, 0, es * vl, st);
     cudaMemsetAsync(L.t2, 0, es * vl, st);
+    L.err = h->d_flag;
+    // FP32 operator input staged by TMA: the V-cycle applies the operator to z (to t2 on the
+    // finest level); tuning decides whether that variant runs
+    if (fp32 && m != o->n_coarse) {
+      int rc = setup_apply_tma(L, (const float *)L.z, m == n ? (const float *)L.t2 : nullptr);
+      if (rc) return fail(rc);
+    }
     if (m == o->n_coarse) break;
   }
   for (size_t l = 0; l + 1 < h->levels.size(); ++l) {
@@ -516,7 +533,8 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_fail(e, "bmg_setup_hierarchy"));
   if (hflag) {
-    set_error(hflag & 1 ? "a Vanka patch matrix is singular" : "the coarsest operator is singular");
+    set_error(hflag & kErrTmaTimeout ? "a bulk-copy wait timed out during tile tuning"
+              : hflag & 1 ? "a Vanka patch matrix is singular" : "the coarsest operator is singular");
     return fail(BMG_ERR_SINGULAR);
   }
   *out = h;
@@ -524,6 +542,17 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
 }
 
 extern "C" int bmg_hierarchy_levels(const bmg_hierarchy *h) { return h ? (int)h->levels.size() : 0; }
+
+extern "C" int bmg_hierarchy_tile(const bmg_hierarchy *h, int level, int kernel) {
+  if (!h || level < 0 || level >= (int)h->levels.size()) return -1;
+  const Level &L = h->levels[level];
+  switch (kernel) {
+    case BMG_PROF_APPLY: return L.tile_apply == 5 && !L.tma ? 0 : L.tile_apply;
+    case BMG_PROF_VANKA: return L.tile_vanka;
+    case BMG_PROF_VANKA_U: return L.tile_vanka_u;
+    default: return -1;
+  }
+}
 
 extern "C" void bmg_destroy_hierarchy(bmg_hierarchy *h) {
   if (!h) return;
@@ -733,6 +762,14 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
     if ((rc = launch_axpy_multi(x, h->Z, ldv, k, h->dres, vl, st))) return rc;
   }
   BMG_CUDA(cudaStreamSynchronize(st));
+  if (h->opts.precision == BMG_FP32) {         // a timed-out TMA wait leaves its CTA's output unset
+    int flag = 0;
+    BMG_CUDA(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & kErrTmaTimeout) {
+      set_error("bmg_fgmres_solve: a bulk-copy wait in the FP32 operator timed out");
+      return BMG_ERR_CUDA;
+    }
+  }
   inf.relres_est = est;
   inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;

@@ -104,6 +104,9 @@ struct TransferTables {
 void build_transfer_tables(TransferTables *t);
 
 // --------------------------------------------------------------------------------------
+struct TmaMaps;                // tensor maps of a level's FP32 operator input (operator.cu)
+constexpr int kErrTmaTimeout = 1 << 16;   // device error flag: a TMA wait ran out
+
 struct Level {
   int n = 0;
   bool owns_coefs = true;      // false for a hierarchy's view of its system's fine level
@@ -144,6 +147,10 @@ struct Level {
   // Tile shape of the operator / Vanka / displacement-Vanka launches on this level, chosen by
   // timing at setup (index into each kernel's candidate list; -1: the CTA-count rule).
   int tile_apply = -1, tile_vanka = -1, tile_vanka_u = -1;
+  // FP32 operator with its input staged by TMA (tile index 5): tensor maps of the level's
+  // work vectors and coefficients, and the device flag a timed-out wait sets
+  TmaMaps *tma = nullptr;
+  int *err = nullptr;
   // Device flag read by every kernel launched for this level (nullptr: always run).  Used by
   // graph-replayed solves: a kernel whose gate holds 0 returns at once.
   const int *gate = nullptr;
@@ -196,6 +203,10 @@ void make_apply_args(const Level &L, const double *x, const double *b, double *y
                      const int *gate, void *dst);
 int launch_apply_batch(const void *d_args, int count, int n, int tile, cudaStream_t st);
 int prepare_apply_batch();
+// Tensor maps for the TMA-staged FP32 operator on inputs xa and xb (either may be NULL);
+// leaves L.tma NULL (and the kernel unused) when they cannot be encoded.
+int setup_apply_tma(Level &L, const float *xa, const float *xb);
+void free_apply_tma(Level &L);
 int default_apply_tile(int n, int count);
 size_t vanka_args_bytes();
 void make_vanka_args(const Level &L, const double *r, double *x, double omega, bool assign,

@@ -7,6 +7,9 @@
 // phase 2 gathers, for every DoF of the tile, the contributions of its triangles (6 for a
 // vertex, 2 for an edge, 1 for a triangle).  No atomics: the result is deterministic.
 // Constrained displacement slots are ignored on input and written as 0.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstring>
 #include <type_traits>
 #include <utility>
@@ -88,18 +91,50 @@ __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T 
   yl[12] = -c.alpha * gu - dww - c.pp * p;
 }
 
+// Where phase 1 reads the input vector and the coefficients: global memory, or a slab of
+// them staged in shared memory by the tensor-memory-accelerator (TMA) loads of
+// apply_tma_kernel.  xv(k, i, j): block k at position (i, j); kv(o, ci, cj): K^{-1} of
+// triangle o of cell (ci, cj); wv(o, k, ci, cj): entry k of its 3 x 3 RT0 mass.
+template <typename T>
+struct GlobalSrc {
+  const T *x, *kinv, *wm;
+  size_t blk;
+  int P;
+  __device__ __forceinline__ T xv(int k, int i, int j) const { return x[k * blk + (size_t)j * P + i]; }
+  __device__ __forceinline__ T kv(int o, int ci, int cj) const {
+    return kinv[(size_t)o * blk + (size_t)cj * P + ci];
+  }
+  __device__ __forceinline__ T wv(int o, int k, int ci, int cj) const {
+    return wm[(size_t)(6 * o + k) * blk + (size_t)cj * P + ci];
+  }
+};
+
+template <int BX, int BY>
+struct SmemSrc {                 // slab: x [10][BY][BX], coefficients [NC][BY - 1][BX]
+  const float *xs, *cs;
+  int x0, y0;                    // grid position of slab element (0, 0)
+  __device__ __forceinline__ float xv(int k, int i, int j) const {
+    return xs[(k * BY + (j - y0)) * BX + (i - x0)];
+  }
+  __device__ __forceinline__ float kv(int o, int ci, int cj) const {
+    return cs[(o * (BY - 1) + (cj - y0)) * BX + (ci - x0)];
+  }
+  __device__ __forceinline__ float wv(int o, int k, int ci, int cj) const {
+    return cs[((6 * o + k) * (BY - 1) + (cj - y0)) * BX + (ci - x0)];
+  }
+};
+
 // Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
-// tiles on the coarse levels so that their work spreads over many SMs).
-template <typename T, int WM, int kTX, int kTY, int NT>
-__device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, int bx, int by, size_t boff) {
+// tiles on the coarse levels so that their work spreads over many SMs).  sy: shared scratch
+// of 26 values per cell of the tile and its halo.
+template <typename T, int WM, int kTX, int kTY, int NT, typename Src>
+__device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src, T (*sy)[26], int bx,
+                                           int by, size_t boff) {
   constexpr int kEX = kTX + 1, kEY = kTY + 1;
   static_assert(NT >= kTX * kTY, "one thread per output position in phase 2");
-  extern __shared__ unsigned char smem_raw[];
-  T(*sy)[26] = reinterpret_cast<T(*)[26]>(smem_raw);
   const Grid g = a.g;
   const int n = g.n, P = g.pitch;
   const size_t blk = g.blk;
-  const T *x = a.x + boff;
   T *y = a.y + boff;
   const int i0 = bx * kTX, j0 = by * kTY;
   const int tid = threadIdx.x;
@@ -117,30 +152,28 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, int bx, int by
       for (int k = 0; k < 13; ++k) yl[k] = 0;
       continue;
     }
-    const size_t c00 = (size_t)cj * P + ci;          // (ci, cj)
     // L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj)
     // U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1)
     const int v0i = ci + o, v0j = cj + o;
     const int v1i = o ? ci : ci + 1, v1j = o ? cj + 1 : cj;
     const int v2i = o ? ci + 1 : ci, v2j = o ? cj : cj + 1;
-    const size_t a0 = (size_t)v0j * P + v0i, a1 = (size_t)v1j * P + v1i, a2 = (size_t)v2j * P + v2i;
     const bool f0 = vfree(v0i, v0j, n), f1 = vfree(v1i, v1j, n), f2 = vfree(v2i, v2j, n);
-    const size_t ev = o ? c00 + 1 : c00;             // v(ci + o, cj)
-    const size_t eh = o ? c00 + P : c00;             // h(ci, cj + o)
+    const int evi = ci + o;                          // v(ci + o, cj)
+    const int ehj = cj + o;                          // h(ci, cj + o)
     const bool bvf = o ? (ci + 1 < n) : (ci > 0);
     const bool bhf = o ? (cj + 1 < n) : (cj > 0);
-    const T u[9] = {f0 ? x[UX * blk + a0] : T(0), f1 ? x[UX * blk + a1] : T(0), f2 ? x[UX * blk + a2] : T(0),
-                    f0 ? x[UY * blk + a0] : T(0), f1 ? x[UY * blk + a1] : T(0), f2 ? x[UY * blk + a2] : T(0),
-                    x[BD * blk + c00], bvf ? x[BV * blk + ev] : T(0), bhf ? x[BH * blk + eh] : T(0)};
-    const T w[3] = {x[WD * blk + c00], x[WV * blk + ev], x[WH * blk + eh]};
-    const T p = x[(o ? PU : PL) * blk + c00];
+    const T u[9] = {f0 ? src.xv(UX, v0i, v0j) : T(0), f1 ? src.xv(UX, v1i, v1j) : T(0), f2 ? src.xv(UX, v2i, v2j) : T(0),
+                    f0 ? src.xv(UY, v0i, v0j) : T(0), f1 ? src.xv(UY, v1i, v1j) : T(0), f2 ? src.xv(UY, v2i, v2j) : T(0),
+                    src.xv(BD, ci, cj), bvf ? src.xv(BV, evi, cj) : T(0), bhf ? src.xv(BH, ci, ehj) : T(0)};
+    const T w[3] = {src.xv(WD, ci, cj), src.xv(WV, evi, cj), src.xv(WH, ci, ehj)};
+    const T p = src.xv(o ? PU : PL, ci, cj);
     T kin = 0;
     T wm[6];
     if (WM == 0) {
-      kin = a.kinv[(size_t)o * blk + c00];
+      kin = src.kv(o, ci, cj);
     } else {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) wm[k] = a.wm[(size_t)(6 * o + k) * blk + c00];
+      for (int k = 0; k < 6; ++k) wm[k] = src.wv(o, k, ci, cj);
     }
     // FP32: orientation as a compile-time constant, so the element coefficients become
     // immediate constant-bank operands (the FP32 pipe would otherwise wait on indexed
@@ -195,7 +228,10 @@ template <typename T, int WM, int kTX, int kTY, int NT>
 __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
   pdl_enter();
   BMG_GATE(a.gate);
-  apply_tile<T, WM, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, (size_t)blockIdx.z * a.bstride);
+  extern __shared__ unsigned char smem_raw[];
+  const size_t boff = (size_t)blockIdx.z * a.bstride;
+  const GlobalSrc<T> src{a.x + boff, a.kinv, a.wm, a.g.blk, a.g.pitch};
+  apply_tile<T, WM, kTX, kTY, NT>(a, src, reinterpret_cast<T(*)[26]>(smem_raw), blockIdx.x, blockIdx.y, boff);
 }
 
 // Batched form: several instances of one grid size in one launch, blockIdx.z selecting the
@@ -206,8 +242,164 @@ template <int kTX, int kTY, int NT>
 __global__ void __launch_bounds__(NT) apply_batch_kernel(const ApplyArgs<double> *__restrict__ args) {
   const ApplyArgs<double> &a = args[blockIdx.z];
   BMG_GATE(a.gate);
-  if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, 0);
-  else apply_tile<double, 0, kTX, kTY, NT>(a, blockIdx.x, blockIdx.y, 0);
+  extern __shared__ unsigned char smem_raw[];
+  double(*sy)[26] = reinterpret_cast<double(*)[26]>(smem_raw);
+  const GlobalSrc<double> src{a.x, a.kinv, a.wm, a.g.blk, a.g.pitch};
+  if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+  else apply_tile<double, 0, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+}
+
+// ---- FP32 operator with TMA-staged input --------------------------------------------------
+// One CTA per 32 x 8 tile.  Thread 0 issues two bulk tensor copies into shared memory: the
+// 10 blocks of x over the tile and its halo (rows j0-1 .. j0+8, columns i0-4 .. i0+35: the
+// start column is rounded down so that it is 16-byte aligned; positions outside the grid
+// arrive as zeros) and the coefficient planes of cells (i0-4 .., j0-1 .. j0+7).  An mbarrier
+// counts the bytes; every thread waits on it (bounded: after the limit the CTA sets the
+// level's error flag, waits once more for its copies and leaves).  Phases 1 and 2 are
+// apply_tile's, reading the slab instead of global memory.
+struct TmaMaps {
+  const void *xptr[2] = {nullptr, nullptr};
+  CUtensorMap x[2];
+  CUtensorMap coef;
+};
+
+constexpr int kTmaTX = 32, kTmaTY = 8, kTmaNT = 256, kTmaBX = 40, kTmaBY = kTmaTY + 2;
+constexpr long long kTmaWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kTmaWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+template <int WM>
+constexpr size_t tma_smem_bytes() {
+  return 128 + sizeof(float) * (10 * kTmaBY * kTmaBX + (WM ? 12 : 2) * (kTmaBY - 1) * kTmaBX +
+                                26 * (kTmaTX + 1) * (kTmaTY + 1));
+}
+
+template <int WM>
+__global__ void __launch_bounds__(kTmaNT) apply_tma_kernel(const __grid_constant__ ApplyArgs<float> a,
+                                                           const __grid_constant__ CUtensorMap tx,
+                                                           const __grid_constant__ CUtensorMap tc,
+                                                           int *err) {
+  constexpr int NC = WM ? 12 : 2;
+  constexpr uint32_t kBytes = sizeof(float) * (10 * kTmaBY * kTmaBX + NC * (kTmaBY - 1) * kTmaBX);
+  pdl_enter();
+  BMG_GATE(a.gate);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  float *xs = reinterpret_cast<float *>(base);
+  float *cs = xs + 10 * kTmaBY * kTmaBX;
+  float(*sy)[26] = reinterpret_cast<float(*)[26]>(cs + NC * (kTmaBY - 1) * kTmaBX);
+  __shared__ alignas(8) unsigned long long bar;
+  const int x0 = blockIdx.x * kTmaTX - 4, y0 = blockIdx.y * kTmaTY - 1;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the input was written by earlier kernels through ordinary stores: order those writes
+    // before the bulk copies' reads (a different memory proxy)
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(kBytes) : "memory");
+    tma_load_3d(smem_u32(xs), &tx, x0, y0, 0, b);
+    tma_load_3d(smem_u32(cs), &tc, x0, y0, 0, b);
+  }
+  const bool ok = mbar_wait_bounded(b, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicOr(err, kErrTmaTimeout);
+    mbar_wait_bounded(b, 0);
+    return;
+  }
+  const SmemSrc<kTmaBX, kTmaBY> src{xs, cs, x0, y0};
+  apply_tile<float, WM, kTmaTX, kTmaTY, kTmaNT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+}
+
+template <int WM>
+static int launch_apply_tma(const ApplyArgs<float> &a, const Level &L, const CUtensorMap &tx,
+                            cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = tma_smem_bytes<WM>();
+  if (!attr) {
+    BMG_CUDA(cudaFuncSetAttribute(apply_tma_kernel<WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid((L.g.pitch + kTmaTX - 1) / kTmaTX, (L.n + 1 + kTmaTY - 1) / kTmaTY);
+  BMG_CUDA(launch_pdl(apply_tma_kernel<WM>, grid, dim3(kTmaNT), smem, st, a, tx, L.tma->coef, L.err));
+  return BMG_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D FP32 map (pitch, rows, planes) with plane stride plane_elems, box (40, box_rows, planes)
+static bool encode_planes(CUtensorMap *m, const void *base, int pitch, int rows, int planes,
+                          size_t plane_elems, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !base) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)plane_elems * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)kTmaBX, (cuuint32_t)box_rows, (cuuint32_t)planes};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int setup_apply_tma(Level &L, const float *xa, const float *xb) {
+  free_apply_tma(L);
+  const float *coef = L.wm_full ? L.wm32 : L.kinv32;
+  if (!coef || L.n < kTmaTX) return BMG_OK;
+  TmaMaps *t = new TmaMaps();
+  bool ok = encode_planes(&t->coef, coef, L.g.pitch, L.n + 1, L.wm_full ? 12 : 2, L.g.blk, kTmaBY - 1);
+  const float *xs[2] = {xa, xb};
+  for (int k = 0; k < 2 && ok; ++k) {
+    if (!xs[k]) continue;
+    ok = encode_planes(&t->x[k], xs[k], L.g.pitch, L.n + 1, NBLK, L.g.blk, kTmaBY);
+    t->xptr[k] = xs[k];
+  }
+  if (ok) L.tma = t;
+  else delete t;
+  return BMG_OK;
+}
+
+void free_apply_tma(Level &L) {
+  delete L.tma;
+  L.tma = nullptr;
 }
 
 template <typename T, int WM, int TX, int TY, int NT>
@@ -240,6 +432,13 @@ static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cud
     case 2: return launch_apply_tile<T, WM, 8, 8, 128>(a, L, batch, st);
     case 3: return launch_apply_tile<T, WM, 8, 4, 96>(a, L, batch, st);
     case 4: return launch_apply_tile<T, WM, 4, 4, 64>(a, L, batch, st);
+    case 5:                         // FP32, input staged by TMA (else the same 32 x 8 tile)
+      if constexpr (sizeof(T) == 4) {
+        if (L.tma && L.err && batch == 1)
+          for (int k = 0; k < 2; ++k)
+            if (L.tma->xptr[k] == (const void *)a.x) return launch_apply_tma<WM>(a, L, L.tma->x[k], st);
+      }
+      return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
     default: break;
   }
   // the largest tile that still gives every SM about two CTAs

@@ -406,39 +406,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   }
   __syncthreads();
   const size_t ld = (size_t)a.nslots;
-  if (!s_mixed && a.klein) {
-    // every patch of the tile is an interior patch of uniform coefficients: solve in the
-    // symmetry-adapted basis.  q = U^T r per patch (into sx), x' = B q by (row, patch) tasks
-    // whose row is uniform across a warp (into sr), x = U x' per patch (into sx).
-    for (int p = tid; p < NP; p += NT) {
-      T r[20], q[20];
-#pragma unroll
-      for (int c = 0; c < 20; ++c) r[c] = sr[p * LD + c];
-      klein_fwd(r, q);
-#pragma unroll
-      for (int c = 0; c < 20; ++c) sx[p * LD + c] = q[c];
-    }
-    __syncthreads();
-    for (int t = tid; t < NP * 20; t += NT) {
-      const int k = t / NP, p = t % NP;
-      const int b0 = klein_block_start(k), bs = klein_block_size(k);
-      const T *q = sx + p * LD + b0;
-      T acc = 0;
-#pragma unroll
-      for (int l = 0; l < 7; ++l)
-        if (l < bs) acc = fma(a.kb[k][l], q[l], acc);
-      sr[p * LD + k] = acc;
-    }
-    __syncthreads();
-    for (int p = tid; p < NP; p += NT) {
-      T q[20], x[20];
-#pragma unroll
-      for (int c = 0; c < 20; ++c) q[c] = sr[p * LD + c];
-      klein_inv(q, x);
-#pragma unroll
-      for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
-    }
-  } else if (!s_mixed) {
+  if (!s_mixed && !a.klein) {
     // every patch of the tile uses the shared interior inverse (slot 0): thread
     // (row = tid % 20, group = tid / 20) keeps its inverse row in registers and sweeps the
     // group's patches, so the solve issues a few shared loads per patch instead of 400
@@ -462,20 +430,58 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       }
     }
   } else {
-    // phase 2 (general): xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads
-    // take consecutive patches of one row, so their inverse loads coalesce (or broadcast)
+    // Patches of slot 0 with the symmetry-adapted inverse (uniform coefficients): q = U^T r
+    // (into sx), x' = B q by (row, patch) tasks (into sr), x = U x' (into sx) -- for every
+    // such patch whatever tile holds it, so results do not depend on the tiling.  Other
+    // patches: x = inverse_slot r by (row, patch) tasks; consecutive threads take
+    // consecutive patches of one row, so their inverse loads coalesce (or broadcast).
+    const bool kl = a.klein != 0;
+    if (kl) {
+      for (int p = tid; p < NP; p += NT) {
+        if (ss[p] != 0) continue;
+        T r[20], q[20];
+#pragma unroll
+        for (int c = 0; c < 20; ++c) r[c] = sr[p * LD + c];
+        klein_fwd(r, q);
+#pragma unroll
+        for (int c = 0; c < 20; ++c) sx[p * LD + c] = q[c];
+      }
+      __syncthreads();
+    }
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
-      const T *inv = a.inv + ss[p];
-      const int rb = sym20_row_base(row);
-      const T *rl = sr + p * LD;
-      T acc = 0;
+      if (kl && ss[p] == 0) {
+        const int b0 = klein_block_start(row), bs = klein_block_size(row);
+        const T *q = sx + p * LD + b0;
+        T acc = 0;
 #pragma unroll
-      for (int c = 0; c < 20; ++c) {
-        const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
-        acc = fma(inv[(size_t)e * ld], rl[c], acc);
+        for (int l = 0; l < 7; ++l)
+          if (l < bs) acc = fma(a.kb[row][l], q[l], acc);
+        sr[p * LD + row] = acc;
+      } else {
+        const T *inv = a.inv + ss[p];
+        const int rb = sym20_row_base(row);
+        const T *rl = sr + p * LD;
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 20; ++c) {
+          const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
+          acc = fma(inv[(size_t)e * ld], rl[c], acc);
+        }
+        sx[p * LD + row] = acc;
       }
-      sx[p * LD + row] = acc;
+    }
+    if (kl) {
+      __syncthreads();
+      for (int p = tid; p < NP; p += NT) {
+        if (ss[p] != 0) continue;
+        T q[20], x[20];
+#pragma unroll
+        for (int c = 0; c < 20; ++c) q[c] = sr[p * LD + c];
+        klein_inv(q, x);
+#pragma unroll
+        for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
+      }
     }
   }
   __syncthreads();
