@@ -2,6 +2,9 @@
 // layout (Dirichlet displacement on the boundary, natural pressure condition).
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "bmg_internal.h"
 
 namespace bmg {
@@ -21,6 +24,17 @@ __device__ __forceinline__ void dof_masks(int i, int j, int n, bool m[NBLK]) {
   m[WH] = in_i;
   m[WV] = in_j;
   m[WD] = m[PL] = m[PU] = in_i && in_j;
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1, so that the body
+// can branch on the index with `if constexpr` and index arrays with constants.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
 }  // namespace bmg

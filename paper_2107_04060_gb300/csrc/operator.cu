@@ -35,17 +35,6 @@ struct ApplyArgs {
 };
 
 
-// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1, so that the body
-// can branch on the index with `if constexpr`.
-template <typename F, int... I>
-__device__ __forceinline__ void static_for_impl(F &f, std::integer_sequence<int, I...>) {
-  (f(std::integral_constant<int, I>{}), ...);
-}
-template <int N, typename F>
-__device__ __forceinline__ void static_for(F &&f) {
-  static_for_impl(f, std::make_integer_sequence<int, N>{});
-}
-
 // Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).  Products with the
 // structural zeros of the element matrices are not formed (Aeps 30 of 81, g 2 of 9, the
 // unit RT0 mass 4 of 9; see kElemNonzeros).

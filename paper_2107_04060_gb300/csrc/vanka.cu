@@ -113,10 +113,10 @@ __host__ __device__ __forceinline__ void klein_inv(const T *q, T *x) {
   x[14] = q[2] + q[14]; x[18] = q[2] - q[14];
 }
 
-__host__ __device__ __forceinline__ int klein_block_start(int k) {
+__host__ __device__ constexpr int klein_block_start(int k) {
   return k < 4 ? 0 : k < 9 ? 4 : k < 16 ? 9 : 16;
 }
-__host__ __device__ __forceinline__ int klein_block_size(int k) {
+__host__ __device__ constexpr int klein_block_size(int k) {
   return k < 4 ? 4 : k < 9 ? 5 : k < 16 ? 7 : 4;
 }
 
@@ -367,46 +367,87 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   const size_t blk = a.g.blk;
   const int i0 = bx * (kPX - 1), j0 = by * (kPY - 1);
   const int tid = threadIdx.x;
-  // phase 1: residual gather, one patch per thread
+  const bool kl = a.klein != 0;
+  // phase 1: residual gather, one patch per thread.  A slot-0 patch with the
+  // symmetry-adapted inverse (uniform coefficients) is solved right here in registers:
+  // q = U^T r, x' = B q (block entries as compile-time parameter operands), x = U x' into sx.
+  // Other patches leave their residual in sr for the (row, patch) tasks below.
   for (int p = tid; p < NP; p += NT) {
     const int pi = i0 + p % kPX, pj = j0 + p / kPX;
-    T *rl = sr + p * LD;
+    T r[20];
+    int sl = 0;
     if (pi <= n && pj <= n) {
-      const T *r = a.r;
+      const T *rv = a.r;
       const size_t o = (size_t)pj * P + pi;
       const bool li = pi >= 1, lj = pj >= 1;
-      rl[0] = r[UX * blk + o];
-      rl[1] = r[UY * blk + o];
-      rl[2] = r[BH * blk + o];                          // E0 = h(pi,pj)
-      rl[8] = r[WH * blk + o];
-      rl[3] = r[BV * blk + o];                          // E1 = v(pi,pj)
-      rl[9] = r[WV * blk + o];
-      rl[4] = li ? r[BH * blk + o - 1] : T(0);          // E2 = h(pi-1,pj)
-      rl[10] = li ? r[WH * blk + o - 1] : T(0);
-      rl[5] = lj ? r[BV * blk + o - P] : T(0);          // E3 = v(pi,pj-1)
-      rl[11] = lj ? r[WV * blk + o - P] : T(0);
-      rl[6] = li ? r[BD * blk + o - 1] : T(0);          // E4 = d(pi-1,pj)
-      rl[12] = li ? r[WD * blk + o - 1] : T(0);
-      rl[7] = lj ? r[BD * blk + o - P] : T(0);          // E5 = d(pi,pj-1)
-      rl[13] = lj ? r[WD * blk + o - P] : T(0);
-      rl[14] = r[PL * blk + o];                         // L(pi,pj)
-      rl[15] = li ? r[PL * blk + o - 1] : T(0);         // L(pi-1,pj)
-      rl[16] = lj ? r[PL * blk + o - P] : T(0);         // L(pi,pj-1)
-      rl[17] = li ? r[PU * blk + o - 1] : T(0);         // U(pi-1,pj)
-      rl[18] = (li && lj) ? r[PU * blk + o - P - 1] : T(0);   // U(pi-1,pj-1)
-      rl[19] = lj ? r[PU * blk + o - P] : T(0);         // U(pi,pj-1)
-      const int sl = a.slot[(size_t)pj * (n + 1) + pi];
-      ss[p] = sl;
-      if (sl != 0) s_mixed = 1;
+      r[0] = rv[UX * blk + o];
+      r[1] = rv[UY * blk + o];
+      r[2] = rv[BH * blk + o];                          // E0 = h(pi,pj)
+      r[8] = rv[WH * blk + o];
+      r[3] = rv[BV * blk + o];                          // E1 = v(pi,pj)
+      r[9] = rv[WV * blk + o];
+      r[4] = li ? rv[BH * blk + o - 1] : T(0);          // E2 = h(pi-1,pj)
+      r[10] = li ? rv[WH * blk + o - 1] : T(0);
+      r[5] = lj ? rv[BV * blk + o - P] : T(0);          // E3 = v(pi,pj-1)
+      r[11] = lj ? rv[WV * blk + o - P] : T(0);
+      r[6] = li ? rv[BD * blk + o - 1] : T(0);          // E4 = d(pi-1,pj)
+      r[12] = li ? rv[WD * blk + o - 1] : T(0);
+      r[7] = lj ? rv[BD * blk + o - P] : T(0);          // E5 = d(pi,pj-1)
+      r[13] = lj ? rv[WD * blk + o - P] : T(0);
+      r[14] = rv[PL * blk + o];                         // L(pi,pj)
+      r[15] = li ? rv[PL * blk + o - 1] : T(0);         // L(pi-1,pj)
+      r[16] = lj ? rv[PL * blk + o - P] : T(0);         // L(pi,pj-1)
+      r[17] = li ? rv[PU * blk + o - 1] : T(0);         // U(pi-1,pj)
+      r[18] = (li && lj) ? rv[PU * blk + o - P - 1] : T(0);   // U(pi-1,pj-1)
+      r[19] = lj ? rv[PU * blk + o - P] : T(0);         // U(pi,pj-1)
+      sl = a.slot[(size_t)pj * (n + 1) + pi];
     } else {
 #pragma unroll
-      for (int c = 0; c < 20; ++c) rl[c] = T(0);
-      ss[p] = 0;
+      for (int c = 0; c < 20; ++c) r[c] = T(0);
+    }
+    ss[p] = sl;
+    if (kl && sl == 0) {
+      T q[20], xq[20], x[20];
+      klein_fwd(r, q);
+      static_for<20>([&](auto k_) {
+        constexpr int k = decltype(k_)::value, b0 = klein_block_start(k);
+        T acc = 0;
+        static_for<klein_block_size(k)>([&](auto l_) {
+          constexpr int l = decltype(l_)::value;
+          acc = fma(a.kb[k][l], q[b0 + l], acc);
+        });
+        xq[k] = acc;
+      });
+      klein_inv(xq, x);
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sr[p * LD + c] = r[c];
+      if (sl != 0) s_mixed = 1;
     }
   }
   __syncthreads();
   const size_t ld = (size_t)a.nslots;
-  if (!s_mixed && !a.klein) {
+  if (kl) {
+    // the tile's other patches (boundary patches with their own inverses)
+    if (s_mixed) {
+      for (int t = tid; t < NP * 20; t += NT) {
+        const int row = t / NP, p = t % NP;
+        if (ss[p] == 0) continue;
+        const T *inv = a.inv + ss[p];
+        const int rb = sym20_row_base(row);
+        const T *rl = sr + p * LD;
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 20; ++c) {
+          const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
+          acc = fma(inv[(size_t)e * ld], rl[c], acc);
+        }
+        sx[p * LD + row] = acc;
+      }
+    }
+  } else if (!s_mixed) {
     // every patch of the tile uses the shared interior inverse (slot 0): thread
     // (row = tid % 20, group = tid / 20) keeps its inverse row in registers and sweeps the
     // group's patches, so the solve issues a few shared loads per patch instead of 400
@@ -430,58 +471,20 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       }
     }
   } else {
-    // Patches of slot 0 with the symmetry-adapted inverse (uniform coefficients): q = U^T r
-    // (into sx), x' = B q by (row, patch) tasks (into sr), x = U x' (into sx) -- for every
-    // such patch whatever tile holds it, so results do not depend on the tiling.  Other
-    // patches: x = inverse_slot r by (row, patch) tasks; consecutive threads take
-    // consecutive patches of one row, so their inverse loads coalesce (or broadcast).
-    const bool kl = a.klein != 0;
-    if (kl) {
-      for (int p = tid; p < NP; p += NT) {
-        if (ss[p] != 0) continue;
-        T r[20], q[20];
-#pragma unroll
-        for (int c = 0; c < 20; ++c) r[c] = sr[p * LD + c];
-        klein_fwd(r, q);
-#pragma unroll
-        for (int c = 0; c < 20; ++c) sx[p * LD + c] = q[c];
-      }
-      __syncthreads();
-    }
+    // phase 2 (general): xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads
+    // take consecutive patches of one row, so their inverse loads coalesce (or broadcast)
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
-      if (kl && ss[p] == 0) {
-        const int b0 = klein_block_start(row), bs = klein_block_size(row);
-        const T *q = sx + p * LD + b0;
-        T acc = 0;
+      const T *inv = a.inv + ss[p];
+      const int rb = sym20_row_base(row);
+      const T *rl = sr + p * LD;
+      T acc = 0;
 #pragma unroll
-        for (int l = 0; l < 7; ++l)
-          if (l < bs) acc = fma(a.kb[row][l], q[l], acc);
-        sr[p * LD + row] = acc;
-      } else {
-        const T *inv = a.inv + ss[p];
-        const int rb = sym20_row_base(row);
-        const T *rl = sr + p * LD;
-        T acc = 0;
-#pragma unroll
-        for (int c = 0; c < 20; ++c) {
-          const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
-          acc = fma(inv[(size_t)e * ld], rl[c], acc);
-        }
-        sx[p * LD + row] = acc;
+      for (int c = 0; c < 20; ++c) {
+        const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
+        acc = fma(inv[(size_t)e * ld], rl[c], acc);
       }
-    }
-    if (kl) {
-      __syncthreads();
-      for (int p = tid; p < NP; p += NT) {
-        if (ss[p] != 0) continue;
-        T q[20], x[20];
-#pragma unroll
-        for (int c = 0; c < 20; ++c) q[c] = sr[p * LD + c];
-        klein_inv(q, x);
-#pragma unroll
-        for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
-      }
+      sx[p * LD + row] = acc;
     }
   }
   __syncthreads();
