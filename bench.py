@@ -56,6 +56,16 @@ def smoother_cases():
 
 
 # ----------------------------------------------------------------------------------------
+def measured_hbm_gbs():
+    """(GB/s, source): the measured copy bandwidth of this GPU model, else the
+    earlier single measurement used as the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (no measured peaks file)"
+
+
 def clocks_sampler(stop_evt, out):
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
            "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -601,6 +611,21 @@ def main():
     stop.set()
     th.join(timeout=5)
     clocks = summarize_clocks(samples)
+    # HBM share of the FP32 V-cycle's fine-level kernels (one profiled FP32 step, outside the
+    # timed region): algorithmic bytes per launch / CUDA-event duration, against the
+    # measured copy bandwidth
+    hbm32 = {}
+    if "fp32" in precisions:
+        peak_gbs, _ = measured_hbm_gbs()
+        for fam in ("apply", "vanka", "vanka_u"):
+            bmg.profile_start(fam, n)
+            one_step("fp32", subset=fp32_cases)
+            torch.cuda.synchronize()
+            r = bmg.profile_stop()
+            if r["launches"]:
+                gbs = BYTES_PER_CELL_F64[fam] * 0.5 * r["cells"] / (r["ms"] * 1e-3) / 1e9
+                hbm32[fam] = {"gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 3),
+                              "avg_launch_ms": round(r["ms"] / r["launches"], 4), "launches": r["launches"]}
 
     # ---- end to end through the host-buffer entry point (FP64 arm)
     hb = {s: torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory() for s in rhs}
@@ -641,7 +666,9 @@ def main():
                           "unit": "MDOF/s", "ms_per_step": ms32,
                           "fp64_same_solves": {"value": sub_dofs / (ms64s * 1e-3) / 1e6, "ms_per_step": ms64s},
                           "speedup_vs_fp64": ms64s / ms32,
-                          "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]]}
+                          "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]],
+                          "vcycle_hbm": {"unit": "GB/s algorithmic, fine level", "peak_gbs": measured_hbm_gbs()[0],
+                                         "peak_source": measured_hbm_gbs()[1], **hbm32}}
     if prof and prof["launches"]:
         avg_ms = prof["ms"] / prof["launches"]
         cells = prof["cells"] / prof["launches"]
