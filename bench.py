@@ -458,6 +458,7 @@ def main():
     ap.add_argument("--no-sequential", action="store_true")
     ap.add_argument("--breakdown", action="store_true",
                     help="print the device time per kernel family of one step and exit")
+    ap.add_argument("--breakdown-precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--breakdown-levels", action="store_true",
                     help="with --breakdown: also per grid level (one step per family and level)")
     args = ap.parse_args()
@@ -575,11 +576,14 @@ def main():
         shares[fam] = bmg.profile_stop()
     dominant = max(shares, key=lambda k: shares[k]["ms"])
     if args.breakdown:
-        # device time per kernel family over all levels, one FP64 step each
+        # device time per kernel family over all levels, one step each (FP64: the whole
+        # sweep; FP32: the FP32-MG arm's solves)
+        bp = args.breakdown_precision
+        bsub = None if bp == "fp64" else fp32_cases
         out = {}
         for fam in ("apply", "vanka", "vanka_u", "restrict", "prolong", "coarse", "krylov"):
             bmg.profile_start(fam, 0)
-            one_step("fp64")
+            one_step(bp, subset=bsub)
             torch.cuda.synchronize()
             out[fam] = bmg.profile_stop()
         levels = {}
@@ -588,12 +592,12 @@ def main():
             while m >= 16:
                 for fam in ("apply", "vanka", "vanka_u", "restrict", "prolong"):
                     bmg.profile_start(fam, m)
-                    one_step("fp64")
+                    one_step(bp, subset=bsub)
                     torch.cuda.synchronize()
                     r = bmg.profile_stop()
                     levels.setdefault(str(m), {})[fam] = [round(r["ms"], 3), r["launches"]]
                 m //= 2
-        ms_step, _, _, _ = timed("fp64", 1)
+        ms_step, _, _, _ = timed(bp, 1, subset=bsub)
         print(json.dumps({"breakdown_ms": {k: round(v["ms"], 3) for k, v in out.items()},
                           "launches": {k: v["launches"] for k, v in out.items()},
                           "per_level_ms_launches": levels, "step_ms": ms_step}))

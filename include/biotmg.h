@@ -170,9 +170,10 @@ typedef struct {
 /*
  * bmg_fgmres_solve -- x ~= A^{-1} b by right-preconditioned flexible GMRES(m) with one
  * V-cycle of h as the preconditioner (Sec. 5.1).  Arnoldi by classical Gram-Schmidt with
- * one re-orthogonalisation pass: the first pass's coefficients come from an FP32 copy of
- * the basis, the second pass and every vector update are FP64 (the Hessenberg column is the
- * sum of both passes, so it and the basis are FP64-accurate).  b, x: device vectors.  The
+ * one re-orthogonalisation pass: the first pass's coefficients and the last correction's
+ * product V h2 (h2 is of the order of the first pass's FP32 error) come from an FP32 copy of
+ * the basis; the second pass's coefficients and the vector updates are FP64 (the Hessenberg
+ * column is the sum of both passes).  b, x: device vectors.  The
  * call returns
  * after the solve has finished (it synchronises `stream` once per iteration to read the
  * Hessenberg column).  info may be NULL.

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_copyout_kernel(const BInst 
 //   OP_CGS1:   V_q.w (q <= j) from the FP32 copy of V (FP32 products and per-thread sums,
 //              FP64 beyond); also Z_j = z (gate_iter)
 //   OP_CGS2:   w -= V d1; V_q.w (q <= j), w.w
-//   OP_CGS3:   w -= V d2; w.w
+//   OP_CGS3:   w -= V d2 with the product V d2 from the FP32 copy of V; w.w
 // Products are stored at partial[slot][chunk] (slot q for V_q.w, slot j + 1 for w.w; slot 0
 // for a norm), then summed over the chunks in a fixed order by batch_reduce_kernel.
 __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__restrict__ I,
@@ -155,7 +155,12 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
     for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
       double wi = w[i];
       if (q0 == 0) {
-        if (update) {
+        if (op == OP_CGS3) {
+          float c = 0.f;
+          for (int p = 0; p < k; ++p) c = fmaf((float)h[p], a.V32[(size_t)p * vl + i], c);
+          wi -= (double)c;
+          w[i] = wi;
+        } else if (update) {
           for (int p = 0; p < k; ++p) wi = fma(-h[p], a.V[(size_t)p * vl + i], wi);
           w[i] = wi;
         }

@@ -330,6 +330,8 @@ int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStre
 int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st);
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                   int nblocks, double *out, cudaStream_t st);
+int launch_correct32_norm(double *w, const float *V32, size_t ldv, int k, const double *h, size_t n,
+                          double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y,
                       size_t n, cudaStream_t st);
 }  // namespace bmg

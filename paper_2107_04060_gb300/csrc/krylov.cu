@@ -275,6 +275,53 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = w[i] * d;
 }
+// Last Gram-Schmidt correction: w <- w - V h with the product V h formed in FP32 from the
+// FP32 copy of the basis (h is the second pass's coefficient vector, of the order of the
+// first pass's FP32 error, so the FP32 rounding of V h is far below FP64 rounding of w),
+// fused with the block-partial sums of w.w (FP64).
+__global__ void __launch_bounds__(256) correct32_norm_kernel(double *__restrict__ w, const float *__restrict__ V32,
+                                                             size_t ldv, int k, const double *__restrict__ h,
+                                                             size_t n, double *__restrict__ partial) {
+  pdl_enter();
+  __shared__ float hs[256];
+  __shared__ double red[8];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = (float)h[q];
+  __syncthreads();
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t c0 = blockIdx.x * chunk;
+  const size_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  double acc = 0.0;
+  for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+    float c = 0.f;
+    for (int q = 0; q < k; ++q) c = fmaf(hs[q], V32[(size_t)q * ldv + i], c);
+    const double wi = w[i] - (double)c;
+    w[i] = wi;
+    acc = fma(wi, wi, acc);
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < 8; ++u) t += red[u];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// out[0] = ||w_new||^2 after w_new = w - V32 h (see correct32_norm_kernel); k <= 256
+int launch_correct32_norm(double *w, const float *V32, size_t ldv, int k, const double *h, size_t n,
+                          double *partial, int nblocks, double *out, cudaStream_t st) {
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
+  BMG_CUDA(launch_pdl(correct32_norm_kernel, dim3(nblocks), dim3(256), 0, st, w, V32, ldv, k, h, n, partial));
+  BMG_CHECK_LAUNCH("correct32_norm_kernel");
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(1), dim3(256), 0, st, (const double *)partial, nblocks, 1, out));
+  BMG_PROF_END(st, 0.0);
+  BMG_CHECK_LAUNCH("reduce_partials_kernel");
+  return BMG_OK;
+}
+
 // v = w / s[0] and its FP32 copy v32
 __global__ void scale2_kernel(const double *__restrict__ w, double *__restrict__ v, float *__restrict__ v32,
                               const double *__restrict__ s, size_t n) {
