@@ -90,7 +90,7 @@ static void free_level(Level &L) {
   cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
   cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
   cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2);
-  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.bry);
+  cudaFree(L.bz); cudaFree(L.bd);
   L = Level();
 }
 
@@ -512,13 +512,11 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
       const double c_fs = p.inv_M + p.alpha * p.alpha / (p.lambda + p.mu);   // 2 mu / d, d = 2
       if (!rc) rc = launch_bsr_setup(L, o->omega_J, c_fs * area, st);
       const size_t vl = vec_len_of(L.n);
-      if (!rc && (cudaMalloc(&L.bz, es * vl) != cudaSuccess || cudaMalloc(&L.bd, es * vl) != cudaSuccess ||
-                  cudaMalloc(&L.bry, es * vl) != cudaSuccess))
+      if (!rc && (cudaMalloc(&L.bz, es * vl) != cudaSuccess || cudaMalloc(&L.bd, es * vl) != cudaSuccess))
         rc = cuda_fail(cudaErrorMemoryAllocation, "BSR work vectors");
       if (!rc) {
         cudaMemsetAsync(L.bz, 0, es * vl, st);
         cudaMemsetAsync(L.bd, 0, es * vl, st);
-        cudaMemsetAsync(L.bry, 0, es * vl, st);
       }
     }
     if (rc) return fail(rc);

@@ -136,7 +136,7 @@ struct Level {
   float *dinv32 = nullptr;
   double *sinv64 = nullptr;    // [2][blk] omega_J / diag(S) per triangle
   float *sinv32 = nullptr;
-  void *bz = nullptr, *bd = nullptr, *bry = nullptr;   // BSR work vectors
+  void *bz = nullptr, *bd = nullptr;   // BSR work vectors
   // coarsest level: dense inverse on the free DoFs
   int nfree = 0;
   int *free_idx = nullptr;     // [nfree] vector positions of the free DoFs

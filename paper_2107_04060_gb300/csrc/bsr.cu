@@ -5,8 +5,9 @@
 //   S  ~= (1/M + alpha^2 / (lambda + 2 mu / d)) M_p + tau B_w D_w^{-1} B_w^T   (d = 2)
 //   z   = F^{-1} r_y;   dp = omega_J diag(S)^{-1} (B z - r_p);   dy = F^{-1}(r_y - B^T dp)
 //   x  <- x + omega (dy, dp)
-// Kernels: (1) z = F^{-1} r_y; (2) dp per triangle; (3) r_y - B^T dp from the coupling
-// terms of the element products alone; (4) dy = F^{-1}(...) fused with the update.
+// Kernels: (1) z = F^{-1} r_y; (2) dp per triangle; (3) dy = F^{-1}(r_y - B^T dp) fused with
+// the update, r_y - B^T dp formed from the coupling terms of the element products alone
+// (alpha g_T dp_T, tau dw_T dp_T) while the residual is gathered.
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
 
@@ -125,7 +126,18 @@ struct VankaUArgs {
   int mode;
   int assign;    // mode 1 only: x was zero, write instead of add
   const int *gate;
+  // mode 1: r is the original residual and r_y - B^T dp is formed on the fly from dp:
+  // + alpha g_T dp_T on the displacement DoFs, + tau dw_T dp_T on the flux DoFs
+  T ag[2][9];    // alpha * g
+  T dwc[2][3];   // tau * dw
 };
+
+// dp of triangle b (PL or PU) of cell (ci, cj); 0 outside the grid
+template <typename T>
+__device__ __forceinline__ T dp_at(const VankaUArgs<T> &a, int b, int ci, int cj) {
+  const int n = a.g.n;
+  return (ci >= 0 && cj >= 0 && ci < n && cj < n) ? a.d[b * a.g.blk + (size_t)cj * a.g.pitch + ci] : T(0);
+}
 
 // kQX x kQY patches per CTA, NT threads; outputs (kQX - 1) x (kQY - 1).  Same three phases
 // as the 20-DoF sweep: residual gather, (patch, row) solve tasks, weighted gather.
@@ -156,6 +168,27 @@ __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ Van
       rl[5] = lj ? r[BV * blk + o - P] : T(0);
       rl[6] = li ? r[BD * blk + o - 1] : T(0);
       rl[7] = lj ? r[BD * blk + o - P] : T(0);
+      if (a.mode == 1) {
+        // r_y - B^T dp: the couplings of the six triangles around the vertex (local vertex 0
+        // of L(pi,pj), U(pi-1,pj-1); 1 of L(pi-1,pj), U(pi,pj-1); 2 of L(pi,pj-1), U(pi-1,pj))
+        // onto its displacement and the bubbles of its six edges; constrained slots stay 0
+        const T dL = dp_at(a, PL, pi, pj), dLw = dp_at(a, PL, pi - 1, pj), dLs = dp_at(a, PL, pi, pj - 1);
+        const T dUw = dp_at(a, PU, pi - 1, pj), dUsw = dp_at(a, PU, pi - 1, pj - 1), dUs = dp_at(a, PU, pi, pj - 1);
+        const bool vf = pi > 0 && pi < n && pj > 0 && pj < n;
+        const bool hf = pj > 0 && pj < n, vvf = pi > 0 && pi < n;
+        if (vf) {
+          rl[0] += a.ag[0][0] * dL + a.ag[0][1] * dLw + a.ag[0][2] * dLs + a.ag[1][2] * dUw +
+                   a.ag[1][0] * dUsw + a.ag[1][1] * dUs;
+          rl[1] += a.ag[0][3] * dL + a.ag[0][4] * dLw + a.ag[0][5] * dLs + a.ag[1][5] * dUw +
+                   a.ag[1][3] * dUsw + a.ag[1][4] * dUs;
+        }
+        if (pi < n && hf) rl[2] += a.ag[0][8] * dL + a.ag[1][8] * dUs;          // h(pi, pj)
+        if (pj < n && vvf) rl[3] += a.ag[0][7] * dL + a.ag[1][7] * dUw;         // v(pi, pj)
+        if (li && hf) rl[4] += a.ag[0][8] * dLw + a.ag[1][8] * dUsw;            // h(pi-1, pj)
+        if (lj && vvf) rl[5] += a.ag[0][7] * dLs + a.ag[1][7] * dUsw;           // v(pi, pj-1)
+        if (li && pj < n) rl[6] += a.ag[0][6] * dLw + a.ag[1][6] * dUw;         // d(pi-1, pj)
+        if (lj && pi < n) rl[7] += a.ag[0][6] * dLs + a.ag[1][6] * dUs;         // d(pi, pj-1)
+      }
       ss[p] = a.slot[(size_t)pj * (n + 1) + pi];
     } else {
 #pragma unroll
@@ -196,9 +229,16 @@ __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ Van
     v[BH] = m[BH] ? h * (X(i, j, 2) + X(i + 1, j, 4)) : T(0);
     v[BV] = m[BV] ? h * (X(i, j, 3) + X(i, j + 1, 5)) : T(0);
     v[BD] = m[BD] ? h * (X(i, j + 1, 7) + X(i + 1, j, 6)) : T(0);
-    v[WH] = m[WH] ? a.dinv[0 * blk + o] * a.r[WH * blk + o] : T(0);
-    v[WV] = m[WV] ? a.dinv[1 * blk + o] * a.r[WV * blk + o] : T(0);
-    v[WD] = m[WD] ? a.dinv[2 * blk + o] * a.r[WD * blk + o] : T(0);
+    T rwh = a.r[WH * blk + o], rwv = a.r[WV * blk + o], rwd = a.r[WD * blk + o];
+    if (a.mode == 1) {            // + tau dw_T dp_T of the two triangles of each edge
+      const T dL = dp_at(a, PL, i, j), dU = dp_at(a, PU, i, j);
+      rwh += a.dwc[0][2] * dL + a.dwc[1][2] * dp_at(a, PU, i, j - 1);
+      rwv += a.dwc[0][1] * dL + a.dwc[1][1] * dp_at(a, PU, i - 1, j);
+      rwd += a.dwc[0][0] * dL + a.dwc[1][0] * dU;
+    }
+    v[WH] = m[WH] ? a.dinv[0 * blk + o] * rwh : T(0);
+    v[WV] = m[WV] ? a.dinv[1 * blk + o] * rwv : T(0);
+    v[WD] = m[WD] ? a.dinv[2 * blk + o] * rwd : T(0);
     if (a.mode == 0) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) a.z[k * blk + o] = v[k];
@@ -271,62 +311,6 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
   }
 }
 
-// r_y - B^T dp on the displacement and flux DoFs (the p blocks are not written): with
-// A (0, 0, dp) = (-alpha g_T dp_T, -tau dw_T dp_T, .) per triangle (the operator's element
-// product at u = w = 0), r_u + alpha sum_T g_T dp_T and r_w + sum_T tau dw_T dp_T over the
-// triangles that hold each DoF (6 for a vertex, 2 for an edge).  Constrained slots get 0.
-template <typename T>
-struct RyArgs {
-  Grid g;
-  const T *r;
-  const T *d;    // dp in the p blocks
-  T *ry;
-  const int *gate;
-  T ag[2][9];    // alpha * g
-  T dw[2][3];    // tau * dw
-};
-
-template <typename T>
-__global__ void bsr_ry_kernel(const __grid_constant__ RyArgs<T> a) {
-  pdl_enter();
-  BMG_GATE(a.gate);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = a.g.n, P = a.g.pitch;
-  const size_t blk = a.g.blk;
-  if (i >= P || j > n) return;
-  const size_t o = (size_t)j * P + i;
-  if (i > n) {                                       // padding columns
-#pragma unroll
-    for (int k = UX; k <= WD; ++k) a.ry[k * blk + o] = T(0);
-    return;
-  }
-  auto dp = [&](int b, int ci, int cj) -> T {        // dp of L (b = PL) or U (b = PU) at cell (ci, cj)
-    return (ci >= 0 && cj >= 0 && ci < n && cj < n) ? a.d[b * blk + (size_t)cj * P + ci] : T(0);
-  };
-  const T pL = dp(PL, i, j), pLw = dp(PL, i - 1, j), pLs = dp(PL, i, j - 1);
-  const T pUw = dp(PU, i - 1, j), pUsw = dp(PU, i - 1, j - 1), pUs = dp(PU, i, j - 1);
-  const T pU = dp(PU, i, j);
-  // vertex (i, j): local vertex 0 of L(i,j) and U(i-1,j-1), 1 of L(i-1,j) and U(i,j-1),
-  // 2 of L(i,j-1) and U(i-1,j)
-  T v[8];
-  v[UX] = a.ag[0][0] * pL + a.ag[0][1] * pLw + a.ag[0][2] * pLs +
-          a.ag[1][2] * pUw + a.ag[1][0] * pUsw + a.ag[1][1] * pUs;
-  v[UY] = a.ag[0][3] * pL + a.ag[0][4] * pLw + a.ag[0][5] * pLs +
-          a.ag[1][5] * pUw + a.ag[1][3] * pUsw + a.ag[1][4] * pUs;
-  // h(i,j): e2 of L(i,j) and U(i,j-1); v(i,j): e1 of L(i,j) and U(i-1,j); d(i,j): e0 of both
-  v[BH] = a.ag[0][8] * pL + a.ag[1][8] * pUs;
-  v[BV] = a.ag[0][7] * pL + a.ag[1][7] * pUw;
-  v[BD] = a.ag[0][6] * pL + a.ag[1][6] * pU;
-  v[WH] = a.dw[0][2] * pL + a.dw[1][2] * pUs;
-  v[WV] = a.dw[0][1] * pL + a.dw[1][1] * pUw;
-  v[WD] = a.dw[0][0] * pL + a.dw[1][0] * pU;
-  bool m[NBLK];
-  dof_masks(i, j, n, m);
-#pragma unroll
-  for (int k = UX; k <= WD; ++k) a.ry[k * blk + o] = m[k] ? a.r[k * blk + o] + v[k] : T(0);
-}
-
 template <typename T, int QX, int QY, int NT>
 static void launch_vanka_u_tile(const VankaUArgs<T> &a, const Level &L, cudaStream_t st) {
   dim3 grid((L.g.pitch + QX - 2) / (QX - 1), (L.n + 1 + QY - 2) / (QY - 1));
@@ -351,6 +335,13 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
   a.mode = mode;
   a.assign = assign ? 1 : 0;
   a.gate = L.gate;
+  {
+    const OpCoefs<T> &c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
+    for (int o = 0; o < 2; ++o) {
+      for (int k = 0; k < 9; ++k) a.ag[o][k] = c.alpha * c.g[o][k];
+      for (int k = 0; k < 3; ++k) a.dwc[o][k] = c.dw[o][k];
+    }
+  }
   auto ctas = [&](int px, int py) {
     return (long long)((L.g.pitch + px - 2) / (px - 1)) * ((L.n + 1 + py - 2) / (py - 1));
   };
@@ -375,13 +366,12 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
 }
 
 // One BSR relaxation x <- x + omega M^{-1} r.  Work vectors of the level: bz (z = F^{-1} r_y),
-// bd (dp in the p blocks; its u and w blocks stay zero), bry (r_y - B^T dp).
+// bd (dp in the p blocks; its u and w blocks stay zero).
 template <typename T>
 int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
   const bool f64 = sizeof(T) == 8;
   T *z = (T *)L.bz;
   T *d = (T *)L.bd;
-  T *ry = (T *)L.bry;
   int rc = launch_vanka_u<T>(L, r, z, nullptr, nullptr, omega, 0, false, st);
   if (rc) return rc;
   DpArgs<T> a;
@@ -397,23 +387,8 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   BMG_CUDA(launch_pdl(bsr_dp_kernel<T>, dim3(gr), dim3(b), 0, st, a));
     BMG_PROF_END(st, 0.0); }
   BMG_CHECK_LAUNCH("bsr_dp_kernel");
-  // r_y - B^T dp on the u and w blocks
-  RyArgs<T> ra;
-  ra.g = L.g;
-  ra.r = r;
-  ra.d = d;
-  ra.ry = ry;
-  ra.gate = L.gate;
-  for (int o = 0; o < 2; ++o) {
-    for (int k = 0; k < 9; ++k) ra.ag[o][k] = a.c.alpha * a.c.g[o][k];
-    for (int k = 0; k < 3; ++k) ra.dw[o][k] = a.c.dw[o][k];
-  }
-  dim3 rb(32, 8), rg((L.g.pitch + 31) / 32, (L.n + 1 + 7) / 8);
-  { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
-  BMG_CUDA(launch_pdl(bsr_ry_kernel<T>, dim3(rg), dim3(rb), 0, st, ra));
-    BMG_PROF_END(st, 0.0); }
-  BMG_CHECK_LAUNCH("bsr_ry_kernel");
-  return launch_vanka_u<T>(L, ry, nullptr, x, d, omega, 1, assign, st);
+  // dy = F^{-1}(r_y - B^T dp) with r_y - B^T dp formed inside the displacement sweep
+  return launch_vanka_u<T>(L, r, nullptr, x, d, omega, 1, assign, st);
 }
 
 template int launch_bsr_sweep<double>(const Level &, const double *, double *, double, cudaStream_t, bool);
