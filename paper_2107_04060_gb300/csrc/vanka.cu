@@ -432,6 +432,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   if (kl) {
     // the tile's other patches (boundary patches with their own inverses)
     if (s_mixed) {
+#pragma unroll 2
       for (int t = tid; t < NP * 20; t += NT) {
         const int row = t / NP, p = t % NP;
         if (ss[p] == 0) continue;
@@ -472,7 +473,9 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
     }
   } else {
     // phase 2 (general): xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads
-    // take consecutive patches of one row, so their inverse loads coalesce (or broadcast)
+    // take consecutive patches of one row, so their inverse loads coalesce (or broadcast);
+    // four tasks per step keep 80 independent factor loads in flight per thread
+#pragma unroll 4
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
       const T *inv = a.inv + ss[p];
