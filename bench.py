@@ -39,6 +39,9 @@ MAXIT = 1000
 # roofline denominators: FP64 FMA pipe (nominal 1.25 TFLOP/s for the GB300; measured
 # 1.20 TFLOP/s with a register FMA loop), HBM from the driver-written measured peaks
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes per fine-level launch of the FP64 operator inside the sweep, from the ncu
+# capture summarised in profiles/launches_fp64_sweep_512.md (null it when the kernel changes)
+APPLY_TRAFFIC_BYTES = 42.8e6
 # algorithmic work per grid cell of the fine-level kernels (derivation in the design doc); the
 # operator counts the nonzero products of the element matrices only (156 flops per triangle)
 FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10}
@@ -680,7 +683,8 @@ def main():
         achieved = flops / (avg_ms * 1e-3) / 1e12
         out["roofline"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
                            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                           "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                           "frac": achieved / FP64_PEAK_TFLOPS,
+                           "traffic": APPLY_TRAFFIC_BYTES if dominant == "apply" else None,
                            "avg_launch_ms": avg_ms, "launches": prof["launches"],
                            "peak_source": "nominal FP64 rate (derivation in DESIGN.md)",
                            "shares_ms": {k: round(v["ms"], 3) for k, v in shares.items()}}
