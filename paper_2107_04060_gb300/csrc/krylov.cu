@@ -134,20 +134,26 @@ __global__ void __launch_bounds__(256) dots32_kernel(const float *__restrict__ V
   pdl_enter();
   constexpr int G = 8;
   __shared__ double red[G][8];
-  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  // groups of 4 elements per thread (16-byte loads); n and ldv are multiples of 4
+  const size_t n4 = n / 4, chunk = (n4 + gridDim.x - 1) / gridDim.x;
   const size_t c0 = blockIdx.x * chunk;
-  const size_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  const size_t c1 = c0 + chunk < n4 ? c0 + chunk : n4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double2 *w2 = reinterpret_cast<const double2 *>(w);
   for (int q0 = 0; q0 < k; q0 += G) {
     const int cnt = (k - q0) < G ? (k - q0) : G;
     float acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = 0.f;
     for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-      const float wi = (float)w[i];
+      const double2 wa = w2[2 * i], wb = w2[2 * i + 1];
+      const float x0 = (float)wa.x, x1 = (float)wa.y, x2 = (float)wb.x, x3 = (float)wb.y;
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        if (g < cnt) acc[g] = fmaf(V[(size_t)(q0 + g) * ldv + i], wi, acc[g]);
+        if (g < cnt) {
+          const float4 v = reinterpret_cast<const float4 *>(V + (size_t)(q0 + g) * ldv)[i];
+          acc[g] = fmaf(v.x, x0, fmaf(v.y, x1, fmaf(v.z, x2, fmaf(v.w, x3, acc[g]))));
+        }
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -287,16 +293,25 @@ __global__ void __launch_bounds__(256) correct32_norm_kernel(double *__restrict_
   __shared__ double red[8];
   for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = (float)h[q];
   __syncthreads();
-  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  // groups of 4 elements per thread (16-byte loads); n and ldv are multiples of 4
+  const size_t n4 = n / 4, chunk = (n4 + gridDim.x - 1) / gridDim.x;
   const size_t c0 = blockIdx.x * chunk;
-  const size_t c1 = c0 + chunk < n ? c0 + chunk : n;
+  const size_t c1 = c0 + chunk < n4 ? c0 + chunk : n4;
+  double2 *w2 = reinterpret_cast<double2 *>(w);
   double acc = 0.0;
   for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-    float c = 0.f;
-    for (int q = 0; q < k; ++q) c = fmaf(hs[q], V32[(size_t)q * ldv + i], c);
-    const double wi = w[i] - (double)c;
-    w[i] = wi;
-    acc = fma(wi, wi, acc);
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < k; ++q) {
+      const float4 v = reinterpret_cast<const float4 *>(V32 + (size_t)q * ldv)[i];
+      const float hq = hs[q];
+      c.x = fmaf(hq, v.x, c.x); c.y = fmaf(hq, v.y, c.y);
+      c.z = fmaf(hq, v.z, c.z); c.w = fmaf(hq, v.w, c.w);
+    }
+    double2 wa = w2[2 * i], wb = w2[2 * i + 1];
+    wa.x -= (double)c.x; wa.y -= (double)c.y; wb.x -= (double)c.z; wb.y -= (double)c.w;
+    w2[2 * i] = wa;
+    w2[2 * i + 1] = wb;
+    acc = fma(wa.x, wa.x, fma(wa.y, wa.y, fma(wb.x, wb.x, fma(wb.y, wb.y, acc))));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
