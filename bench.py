@@ -233,6 +233,23 @@ def batched_instances(count: int, seed: int = 2026):
     return out
 
 
+def shard_instances(count: int, rank: int, world: int):
+    """Instances of the batched workload solved by `rank` of `world` (round robin: every
+    instance on exactly one rank, sizes spread evenly); no data crosses ranks."""
+    return [q for q in range(count) if q % world == rank]
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_batched(args):
     """Batched workload: every instance solved to 1e-8 by one graph launch of the batched
     FGMRES, timed against the same instances solved one after the other with the
@@ -241,9 +258,17 @@ def run_batched(args):
     import torch
     import paper_2107_04060_gb300 as bmg
     import synthetic
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    inst = batched_instances(args.batch_count)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    all_inst = batched_instances(args.batch_count)
+    inst = [all_inst[q] for q in shard_instances(len(all_inst), rank, world)]
+    ndof_all = sum(bmg.free_dofs(c["n"]) for c in all_inst)
     t0 = time.perf_counter()
     systems, hs, bs = [], [], []
     for c in inst:
@@ -268,6 +293,8 @@ def run_batched(args):
     times = []
     for _ in range(args.steps):
         flush.fill_(1.0)
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         l0 = bmg.launch_count()
         ev0.record()
@@ -275,14 +302,14 @@ def run_batched(args):
         ev1.record()
         torch.cuda.synchronize()
         launches = bmg.launch_count() - l0
-        times.append(ev0.elapsed_time(ev1))
+        times.append(max_over_ranks(ev0.elapsed_time(ev1), world, dev))
     bad = [i for i in infos if i["status"] != "converged"]
     if bad:
         raise RuntimeError(f"batched solve: {len(bad)} instances did not converge")
     # the same instances one after the other (single-instance FGMRES, host-driven)
     seq_ms = None
     seq_iters = []
-    if not args.no_sequential:
+    if not args.no_sequential and world == 1:
         x = [torch.zeros_like(b) for b in bs]
         for q in range(min(3, len(hs))):
             hs[q].fgmres_solve(bs[q], x[q], rtol=RTOL, restart=RESTART, maxit=MAXIT)
@@ -298,12 +325,15 @@ def run_batched(args):
     ms = float(np.median(times))
     iters = [i["iters"] for i in infos]
     sizes = sorted({c["n"] for c in inst})
+    if rank != 0:
+        return
     print(json.dumps({
         "workload": f"batched {len(inst)} instances, n in {{32,64,128,256}}, lambda log-uniform [1,1e6], "
                     "lognormal K sigma 1, FP64 Vanka V(1,1) FGMRES(50) to 1e-8",
         "metric": "MDOF/s to 1e-8 rel. residual (batched)", "unit": "MDOF/s",
-        "value": ndof / (ms * 1e-3) / 1e6, "ms_per_solve": ms, "steps": args.steps,
-        "warmup": args.warmup, "free_dofs": ndof,
+        "value": ndof_all / (ms * 1e-3) / 1e6, "ms_per_solve": ms, "steps": args.steps,
+        "warmup": args.warmup, "free_dofs": ndof_all, "n_gpus": world,
+        "scaling": "strong (instances split round robin across ranks, no data-path collective)",
         "sequential_ms": seq_ms,
         "sequential_mdofs": (ndof / (seq_ms * 1e-3) / 1e6) if seq_ms else None,
         "speedup_vs_sequential": (seq_ms / ms) if seq_ms else None,
