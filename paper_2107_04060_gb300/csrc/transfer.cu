@@ -56,14 +56,16 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
   rc[ct * gc.blk + o] = acc;
 }
 
-// One thread per (fine position, DoF type): blockIdx.z is the type.
+// One thread per (fine position, DoF type): blockIdx.z is the type.  threadIdx.y is the parity
+// class (i & 1) + 2 (j & 1) of the position, so every warp reads one stencil table and runs one
+// loop length (block 32 x 4 covers 64 fine columns of two fine rows).
 template <typename T>
 __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__restrict__ xf,
                                const int *gate) {
   pdl_enter();
   BMG_GATE(gate);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (threadIdx.y & 1);
+  const int j = 2 * blockIdx.y + (threadIdx.y >> 1);
   const int t = blockIdx.z;
   const int nf = gf.n, nc = gc.n;
   if (i > nf || j > nf) return;
@@ -99,7 +101,7 @@ template <typename T>
 int launch_prolong_add(const Level &fine, const Level &coarse, const T *xc, T *xf,
                        cudaStream_t st) {
   dim3 block(32, 4);
-  dim3 grid((fine.n + 1 + 31) / 32, (fine.n + 1 + 3) / 4, NBLK);
+  dim3 grid((fine.n + 1 + 63) / 64, (fine.n + 1 + 1) / 2, NBLK);
   { BMG_PROF_BEGIN(BMG_PROF_PROLONG, fine.n, st);
   BMG_CUDA(launch_pdl(prolong_kernel<T>, dim3(grid), dim3(block), 0, st, fine.g, coarse.g, xc, xf, fine.gate));
     BMG_PROF_END(st, (double)fine.n * fine.n); }
@@ -139,8 +141,8 @@ __global__ void prolong_batch_kernel(const TransferArgs *__restrict__ args) {
   const TransferArgs &a = args[blockIdx.z / NBLK];
   BMG_GATE(a.gate);
   const Grid gf = a.gf, gc = a.gc;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + (threadIdx.y & 1);   // parity per warp
+  const int j = 2 * blockIdx.y + (threadIdx.y >> 1);
   const int t = blockIdx.z % NBLK;
   const int nf = gf.n, nc = gc.n;
   if (i > nf || j > nf) return;
@@ -174,7 +176,7 @@ int launch_restrict_batch(const TransferArgs *d_args, int count, int nf, cudaStr
 int launch_prolong_batch(const TransferArgs *d_args, int count, int nf, cudaStream_t st) {
   if (count <= 0) return BMG_OK;
   dim3 block(32, 4);
-  dim3 grid((nf + 1 + 31) / 32, (nf + 1 + 3) / 4, NBLK * count);
+  dim3 grid((nf + 1 + 63) / 64, (nf + 1 + 1) / 2, NBLK * count);
   prolong_batch_kernel<<<grid, block, 0, st>>>(d_args);
   BMG_CHECK_LAUNCH("prolong_batch_kernel");
   return BMG_OK;
