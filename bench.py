@@ -44,8 +44,9 @@ FP64_PEAK_TFLOPS = 1.25
 APPLY_TRAFFIC_BYTES = 42.8e6
 # algorithmic work per grid cell of the fine-level kernels (derivation in the design doc); the
 # operator counts the nonzero products of the element matrices only (156 flops per triangle)
-FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10}
-BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208}
+FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10,
+                  "restrict": 0, "prolong": 0}
+BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208, "restrict": 100, "prolong": 180}
 
 
 def smoother_cases():
@@ -189,7 +190,7 @@ def run_micro(args):
     y = torch.empty_like(x)
     h = None
     if args.micro != "apply":
-        h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision=args.precision)
+        h = bmg.setup_hierarchy(s, args.smoother, 1, 1, omega=0.7, precision=args.precision)
     fam = {"apply": "apply", "vanka": "vanka", "vcycle": args.family or "vanka"}[args.micro]
     def run():
         if args.micro == "apply":
@@ -477,7 +478,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--uniform-k", action="store_true", help="--micro: constant K instead of lognormal")
-    ap.add_argument("--family", default=None, choices=["apply", "vanka"],
+    ap.add_argument("--smoother", default="vanka", choices=["vanka", "bsr"], help="--micro vcycle: smoother")
+    ap.add_argument("--family", default=None, choices=["apply", "vanka", "vanka_u", "restrict", "prolong"],
                     help="--micro vcycle: kernel family to time (default vanka)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint"],
                     help="sweep: the 512^2 parameter sweep (default); batched / mixed / adjoint: "

@@ -354,7 +354,9 @@ struct VankaSweepArgs {
   T kb[20][7];
 };
 
-template <typename T, int kPX, int kPY, int NT>
+// kKlein = false compiles the symmetry-adapted path out (slot-0 patches then use the dense
+// inverse, which is always stored): fewer registers where that path is not used.
+template <typename T, int kPX, int kPY, int NT, bool kKlein = true>
 __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, int by) {
   constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
   __shared__ T sr[NP * LD];
@@ -367,7 +369,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   const size_t blk = a.g.blk;
   const int i0 = bx * (kPX - 1), j0 = by * (kPY - 1);
   const int tid = threadIdx.x;
-  const bool kl = a.klein != 0;
+  const bool kl = kKlein && a.klein != 0;
   // phase 1: residual gather, one patch per thread.  A slot-0 patch with the
   // symmetry-adapted inverse (uniform coefficients) is solved right here in registers:
   // q = U^T r, x' = B q (block entries as compile-time parameter operands), x = U x' into sx.
@@ -406,7 +408,11 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       for (int c = 0; c < 20; ++c) r[c] = T(0);
     }
     ss[p] = sl;
-    if (kl && sl == 0) {
+    if constexpr (!kKlein) {
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sr[p * LD + c] = r[c];
+      if (sl != 0) s_mixed = 1;
+    } else if (kl && sl == 0) {
       T q[20], xq[20], x[20];
       klein_fwd(r, q);
       static_for<20>([&](auto k_) {
@@ -474,8 +480,10 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   } else {
     // phase 2 (general): xhat[p][row] = sum_c inv_slot[row][c] r_p[c]; consecutive threads
     // take consecutive patches of one row, so their inverse loads coalesce (or broadcast);
-    // four tasks per step keep 80 independent factor loads in flight per thread
-#pragma unroll 4
+    // in FP32 four tasks per step keep 80 independent factor loads in flight per thread (the
+    // FP64 sweep is bound by the FP64 pipe instead and keeps its registers)
+    constexpr int kUnroll = sizeof(T) == 4 ? 4 : 1;
+#pragma unroll kUnroll
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
       const T *inv = a.inv + ss[p];
@@ -543,7 +551,7 @@ template <int kPX, int kPY, int NT>
 __global__ void __launch_bounds__(NT) vanka_batch_kernel(const VankaSweepArgs<double> *__restrict__ args) {
   const VankaSweepArgs<double> &a = args[blockIdx.z];
   BMG_GATE(a.gate);
-  vanka_tile<double, kPX, kPY, NT>(a, blockIdx.x, blockIdx.y);
+  vanka_tile<double, kPX, kPY, NT, false>(a, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, int PX, int PY, int NT>
