@@ -8,9 +8,13 @@ each solved with a Vanka V(1,1) and an inexact Braess-Sarazin V(1,1) preconditio
 12 plain FP64 solves.  A second arm ("fp32_mg") times the 8 solves with lambda <= 1e4 with
 FP32 V-cycles inside FP64 FGMRES against the same 8 solves with FP64 V-cycles (at
 lambda/mu = 1e6 an FP32 V-cycle cannot converge: FP32 rounding of a nearly divergence-free
-displacement, times lambda, is a 6% error in the grad-div term).  Setup (assembly, hierarchy, factorisations) is outside the
-timed region; every input is resident in HBM when it starts.  L2 (129 MB) is flushed by a
-256 MB write between solves.
+displacement, times lambda, is a 6% error in the grad-div term).  The solves of a step are
+independent: they run on --streams concurrent CUDA streams (default 4; one host thread each,
+longest solves first), so the latency-bound phases of one solve (small grids, the host read
+of each Arnoldi column) overlap the full-GPU kernels of another.  Setup (assembly,
+hierarchy, factorisations) is outside the timed region; every input is resident in HBM when
+it starts.  L2 (129 MB) is flushed by a 256 MB write before every step (between solves with
+--streams 1).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): replicas only -- every rank runs the whole workload on its own GPU.
@@ -491,6 +495,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="solves of a step run concurrently on this many CUDA streams")
     ap.add_argument("--breakdown", action="store_true",
                     help="print the device time per kernel family of one step and exit")
     ap.add_argument("--breakdown-precision", default="fp64", choices=["fp64", "fp32"])
@@ -564,19 +570,71 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one_step(prec, record=None, subset=None):
-        for ci, c in enumerate(cases):
-            if subset is not None and ci not in subset:
-                continue
-            flush.fill_(float(ci))
-            info = hier[prec, ci].fgmres_solve(rhs[c["seed"]], x, rtol=RTOL, restart=RESTART,
-                                               maxit=MAXIT, x0_is_zero=True)
-            if info["status"] != "converged":
-                raise RuntimeError(f"solve did not converge: {c} {info}")
-            if record is not None:
-                record.append((c, info))
+    nstreams = max(1, args.streams)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
+    xs = [torch.zeros(bmg.vector_len(n), dtype=torch.float64, device=dev) for _ in range(nstreams)]
+    cost = {}                       # iterations seen per case: longest solves start first
 
-    def timed(prec, steps, profile=None, subset=None):
+    def one_step(prec, record=None, subset=None, nstreams=nstreams, solve=None):
+        """One step: the solves of `cases` (or `subset`), on nstreams concurrent streams.
+        solve(ci, k, stream) -> info overrides the device-buffer solve (used by e2e)."""
+        todo = [ci for ci in range(len(cases)) if subset is None or ci in subset]
+        if nstreams == 1 and solve is None:
+            for ci in todo:
+                c = cases[ci]
+                flush.fill_(float(ci))
+                info = hier[prec, ci].fgmres_solve(rhs[c["seed"]], x, rtol=RTOL, restart=RESTART,
+                                                   maxit=MAXIT, x0_is_zero=True)
+                if info["status"] != "converged":
+                    raise RuntimeError(f"solve did not converge: {c} {info}")
+                cost[ci] = info["iters"]
+                if record is not None:
+                    record.append((c, info))
+            return
+        # independent solves on nstreams streams, one host thread each (the library calls
+        # release the interpreter lock); L2 flushed once before the step
+        flush.fill_(1.0)
+        cur = torch.cuda.current_stream()
+        for st_ in streams:
+            st_.wait_stream(cur)
+        todo.sort(key=lambda ci: -cost.get(ci, 0))
+        lock, errors, done = threading.Lock(), [], []
+
+        def worker(k):
+            try:
+                while True:
+                    with lock:
+                        if not todo:
+                            return
+                        ci = todo.pop(0)
+                    c = cases[ci]
+                    info = solve(ci, k, streams[k])
+                    if info["status"] != "converged":
+                        raise RuntimeError(f"solve did not converge: {c} {info}")
+                    with lock:
+                        cost[ci] = info["iters"]
+                        done.append((ci, c, info))
+            except Exception as e:          # reported by the caller
+                errors.append(e)
+
+        if solve is None:
+            def solve(ci, k, stream):
+                c = cases[ci]
+                return hier[prec, ci].fgmres_solve(rhs[c["seed"]], xs[k], rtol=RTOL, restart=RESTART,
+                                                   maxit=MAXIT, x0_is_zero=True, stream=stream)
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(nstreams)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        for st_ in streams:
+            cur.wait_stream(st_)
+        if errors:
+            raise errors[0]
+        if record is not None:
+            record.extend((c, info) for _, c, info in sorted(done, key=lambda d: d[0]))
+
+    def timed(prec, steps, profile=None, subset=None, ns=None):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         recs = []
         barrier()
@@ -586,7 +644,7 @@ def main():
         torch.cuda.nvtx.range_push("timed")
         ev0.record(st)
         for _ in range(steps):
-            one_step(prec, recs, subset)
+            one_step(prec, recs, subset, nstreams=ns or nstreams)
         ev1.record(st)
         torch.cuda.nvtx.range_pop()
         barrier()
@@ -643,6 +701,12 @@ def main():
     th = threading.Thread(target=clocks_sampler, args=(stop, samples), daemon=True)
     th.start()
     ms64, recs64, prof, launches = timed("fp64", args.steps, profile=dominant)
+    # the same kernel family timed on one step with the solves run one after the other (each
+    # launch then has the GPU to itself; in the timed region launches of concurrent solves
+    # share it, which lengthens every launch)
+    prof_iso = None
+    if nstreams > 1:
+        _, _, prof_iso, _ = timed("fp64", 1, profile=dominant, ns=1)
     ms32 = None
     if "fp32" in precisions:
         ms32, recs32, _, _ = timed("fp32", args.steps, subset=fp32_cases)
@@ -658,7 +722,7 @@ def main():
         peak_gbs, _ = measured_hbm_gbs()
         for fam in ("apply", "vanka", "vanka_u"):
             bmg.profile_start(fam, n)
-            one_step("fp32", subset=fp32_cases)
+            one_step("fp32", subset=fp32_cases, nstreams=1)      # kernels alone on the GPU
             torch.cuda.synchronize()
             r = bmg.profile_stop()
             if r["launches"]:
@@ -667,16 +731,21 @@ def main():
                               "avg_launch_ms": round(r["ms"] / r["launches"], 4), "launches": r["launches"]}
 
     # ---- end to end through the host-buffer entry point (FP64 arm)
+    # (the same concurrent step; every solve copies its right-hand side in from pinned host
+    # memory and its solution out inside the timed region)
     hb = {s: torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory() for s in rhs}
     for s in rhs:
         hb[s].copy_(rhs[s].cpu())
-    hx = torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory()
+    hxs = [torch.empty(bmg.vector_len(n), dtype=torch.float64).pin_memory() for _ in range(nstreams)]
+
+    def solve_host(ci, k, stream):
+        c = cases[ci]
+        return hier["fp64", ci].fgmres_solve_host(hb[c["seed"]].numpy(), hxs[k].numpy(), rtol=RTOL,
+                                                  restart=RESTART, maxit=MAXIT, stream=stream)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for ci, c in enumerate(cases):
-            hier["fp64", ci].fgmres_solve_host(hb[c["seed"]].numpy(), hx.numpy(), rtol=RTOL,
-                                                restart=RESTART, maxit=MAXIT)
+        one_step("fp64", solve=solve_host)
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     vec_bytes = bmg.vector_len(n) * 8
@@ -691,7 +760,9 @@ def main():
         "config": {"workload": f"biot-rq {n}x{n} sweep: lambda {list(LAMBDAS)} x K {list(KS)}, "
                                f"Vanka + BSR V(1,1), 12 FP64 solves to 1e-8",
                    "n": n, "free_dofs": nfree, "solves_per_step": len(cases), "inv_M": INV_M,
-                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between solves",
+                   "parallelism": f"replicas x{world}, {nstreams} concurrent solves per GPU",
+                   "l2": ("flushed (256 MB write) before every step" if nstreams > 1
+                          else "flushed (256 MB write) between solves"),
                    "iters": [r[1]["iters"] for r in recs64[:len(cases)]],
                    "setup_s": round(setup_s, 3)},
         "gpu_launches": launches,
@@ -708,18 +779,28 @@ def main():
                           "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]],
                           "vcycle_hbm": {"unit": "GB/s algorithmic, fine level", "peak_gbs": measured_hbm_gbs()[0],
                                          "peak_source": measured_hbm_gbs()[1], **hbm32}}
+    def roofline_of(p):
+        avg_ms = p["ms"] / p["launches"]
+        cells = p["cells"] / p["launches"]
+        achieved = FLOPS_PER_CELL[dominant] * cells / (avg_ms * 1e-3) / 1e12
+        return achieved, avg_ms
     if prof and prof["launches"]:
-        avg_ms = prof["ms"] / prof["launches"]
-        cells = prof["cells"] / prof["launches"]
-        flops = FLOPS_PER_CELL[dominant] * cells
-        achieved = flops / (avg_ms * 1e-3) / 1e12
+        achieved, avg_ms = roofline_of(prof)
         out["roofline"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
                            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS,
                            "traffic": APPLY_TRAFFIC_BYTES if dominant == "apply" else None,
                            "avg_launch_ms": avg_ms, "launches": prof["launches"],
                            "peak_source": "nominal FP64 rate (derivation in DESIGN.md)",
+                           "timed_region": f"{nstreams} concurrent solves: launches share the GPU",
                            "shares_ms": {k: round(v["ms"], 3) for k, v in shares.items()}}
+        if prof_iso and prof_iso["launches"]:
+            a_iso, ms_iso = roofline_of(prof_iso)
+            out["roofline_isolated"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
+                                        "achieved": a_iso, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": a_iso / FP64_PEAK_TFLOPS, "avg_launch_ms": ms_iso,
+                                        "launches": prof_iso["launches"],
+                                        "how": "one extra step, solves one after the other"}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             r = oracle_sample(64, cases)

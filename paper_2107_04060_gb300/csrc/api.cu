@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -15,7 +16,7 @@
 namespace bmg {
 
 static thread_local std::string g_last_error;
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -95,26 +96,32 @@ static void free_level(Level &L) {
 }
 
 // ---- kernel timing ---------------------------------------------------------------------
+// Launches may come from several host threads (solves on distinct handles): each launch keeps
+// its own begin event and appends the (begin, end) pair under a lock.
 struct ProfState {
   int kernel = 0, n = 0;
   std::vector<cudaEvent_t> ev;     // pairs (begin, end)
   double cells = 0.0;
 };
 static ProfState g_prof;
+static std::mutex g_prof_mutex;
 
 bool prof_on(int kernel, int n) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
   return g_prof.kernel != 0 && g_prof.kernel == kernel && (g_prof.n == 0 || g_prof.n == n);
 }
-void prof_begin(cudaStream_t st) {
-  cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return;
+cudaEvent_t prof_begin(cudaStream_t st) {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   cudaEventRecord(e, st);
-  g_prof.ev.push_back(e);
+  return e;
 }
-void prof_end(cudaStream_t st, double cells) {
-  cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return;
+void prof_end(cudaStream_t st, cudaEvent_t e0, double cells) {
+  cudaEvent_t e = nullptr;
+  if (!e0 || cudaEventCreate(&e) != cudaSuccess) return;
   cudaEventRecord(e, st);
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  g_prof.ev.push_back(e0);
   g_prof.ev.push_back(e);
   g_prof.cells += cells;
 }
@@ -123,10 +130,11 @@ void prof_end(cudaStream_t st, double cells) {
 
 using namespace bmg;
 
-extern "C" long long bmg_launch_count(void) { return g_launches; }
+extern "C" long long bmg_launch_count(void) { return g_launches.load(); }
 
 extern "C" int bmg_profile_start(int kernel, int n) {
   if (kernel < 1 || kernel > 7 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
   for (auto e : g_prof.ev) cudaEventDestroy(e);
   g_prof = ProfState();
   g_prof.kernel = kernel;
@@ -135,6 +143,7 @@ extern "C" int bmg_profile_start(int kernel, int n) {
 }
 
 extern "C" int bmg_profile_stop(double *total_ms, long long *launches, double *cells) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
   double tot = 0.0;
   long long cnt = 0;
   cudaError_t err = cudaSuccess;

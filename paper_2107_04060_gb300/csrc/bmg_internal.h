@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -273,7 +275,9 @@ int cuda_fail(cudaError_t e, const char *what);
   } while (0)
 
 namespace bmg {
-extern long long g_launches;   // kernels launched by this library (host-side count)
+// kernels launched by this library (host-side count; solves on distinct handles may run on
+// several host threads at once)
+extern std::atomic<long long> g_launches;
 }
 #define BMG_CHECK_LAUNCH(what)                                       \
   do {                                                               \
@@ -285,12 +289,13 @@ extern long long g_launches;   // kernels launched by this library (host-side co
 // ---- kernel timing (bmg_profile_start / bmg_profile_stop) ------------------------------
 namespace bmg {
 bool prof_on(int kernel, int n);
-void prof_begin(cudaStream_t st);
-void prof_end(cudaStream_t st, double cells);
+cudaEvent_t prof_begin(cudaStream_t st);
+void prof_end(cudaStream_t st, cudaEvent_t e0, double cells);
 }  // namespace bmg
 
-#define BMG_PROF_BEGIN(kid, n, st) const bool prof_ = bmg::prof_on(kid, n); if (prof_) bmg::prof_begin(st)
-#define BMG_PROF_END(st, cells) if (prof_) bmg::prof_end(st, cells)
+#define BMG_PROF_BEGIN(kid, n, st) \
+  const bool prof_ = bmg::prof_on(kid, n); cudaEvent_t prof_e0_ = prof_ ? bmg::prof_begin(st) : nullptr
+#define BMG_PROF_END(st, cells) if (prof_) bmg::prof_end(st, prof_e0_, cells)
 
 // ---- kernel launchers (implemented in the .cu files) -----------------------------------
 namespace bmg {
