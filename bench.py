@@ -9,7 +9,7 @@ each solved with a Vanka V(1,1) and an inexact Braess-Sarazin V(1,1) preconditio
 FP32 V-cycles inside FP64 FGMRES against the same 8 solves with FP64 V-cycles (at
 lambda/mu = 1e6 an FP32 V-cycle cannot converge: FP32 rounding of a nearly divergence-free
 displacement, times lambda, is a 6% error in the grad-div term).  The solves of a step are
-independent: they run on --streams concurrent CUDA streams (default 4; one host thread each,
+independent: they run on --streams concurrent CUDA streams (default 6; one host thread each,
 longest solves first), so the latency-bound phases of one solve (small grids, the host read
 of each Arnoldi column) overlap the full-GPU kernels of another.  Setup (assembly,
 hierarchy, factorisations) is outside the timed region; every input is resident in HBM when
@@ -495,7 +495,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-sequential", action="store_true")
-    ap.add_argument("--streams", type=int, default=4,
+    ap.add_argument("--streams", type=int, default=6,
                     help="solves of a step run concurrently on this many CUDA streams")
     ap.add_argument("--breakdown", action="store_true",
                     help="print the device time per kernel family of one step and exit")
