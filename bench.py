@@ -41,13 +41,15 @@ RTOL = 1e-8
 RESTART = 50
 MAXIT = 1000
 # roofline denominators: FP64 FMA pipe (nominal 1.25 TFLOP/s for the GB300; measured
-# 1.20 TFLOP/s with a register FMA loop), HBM from the driver-written measured peaks
+# 1.20 TFLOP/s with a register FMA loop), HBM from the measured-peaks file of this GPU model
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per fine-level launch of the FP64 operator inside the sweep, from the ncu
 # capture summarised in profiles/launches_fp64_sweep_512.md (null it when the kernel changes)
 APPLY_TRAFFIC_BYTES = 42.8e6
-# algorithmic work per grid cell of the fine-level kernels (derivation in the design doc); the
-# operator counts the nonzero products of the element matrices only (156 flops per triangle)
+# algorithmic work per grid cell of the fine-level kernels: the operator counts the nonzero
+# products of the element matrices (156 flops per triangle, two triangles per cell, plus 26
+# for the gather and the residual); Vanka: the 20 x 20 inverse (400 FMAs) plus the weighted
+# gather; BSR's displacement sweep: the 8 x 8 inverse plus the gather
 FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10,
                   "restrict": 0, "prolong": 0}
 BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208, "restrict": 100, "prolong": 180}
@@ -65,7 +67,7 @@ def smoother_cases():
 
 # ----------------------------------------------------------------------------------------
 def measured_hbm_gbs():
-    """(GB/s, source): the driver-measured copy bandwidth of this GPU model, else the
+    """(GB/s, source): the measured copy bandwidth of this GPU model, else the
     earlier single measurement used as the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -791,7 +793,7 @@ def main():
                            "frac": achieved / FP64_PEAK_TFLOPS,
                            "traffic": APPLY_TRAFFIC_BYTES if dominant == "apply" else None,
                            "avg_launch_ms": avg_ms, "launches": prof["launches"],
-                           "peak_source": "nominal FP64 rate (derivation in DESIGN.md)",
+                           "peak_source": "nominal FP64 rate of the GB300 (1.25 TFLOP/s; a register-FMA loop measured 1.20)",
                            "timed_region": f"{nstreams} concurrent solves: launches share the GPU",
                            "shares_ms": {k: round(v["ms"], 3) for k, v in shares.items()}}
         if prof_iso and prof_iso["launches"]:
