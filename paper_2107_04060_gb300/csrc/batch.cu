@@ -28,11 +28,13 @@
 #include <vector>
 
 #include "bmg_internal.h"
+#include "kernels_common.cuh"
 
 namespace bmg {
 
 constexpr int kChunk = 4096;          // elements of a vector item (256 threads x 16)
 constexpr int kVecThreads = 256;
+constexpr int kMaxBasis = 201;        // basis vectors of one Arnoldi cycle (restart <= 200)
 
 struct BState {
   int gate_iter;      // 1: take an Arnoldi step this trip
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_copyout_kernel(const BInst 
 //   OP_NORM_B: b.b                       OP_NORM_R: r.r (gate_end)
 //   OP_CGS1:   V_q.w (q <= j) from the FP32 copy of V (FP32 products and per-thread sums,
 //              FP64 beyond); also Z_j = z (gate_iter)
-//   OP_CGS2:   w -= V d1; V_q.w (q <= j), w.w
+//   OP_CGS2:   w -= V d1 (FP64); V_q.w (q <= j) from the FP32 copy of V (FP32 products), w.w
 //   OP_CGS3:   w -= V d2 with the product V d2 from the FP32 copy of V; w.w
 // Products are stored at partial[slot][chunk] (slot q for V_q.w, slot j + 1 for w.w; slot 0
 // for a norm), then summed over the chunks in a fixed order by batch_reduce_kernel.
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) acc[gi] = 0.f;
       for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
-        const float wi = (float)w[i];
+        const float wi = f64_to_f32_trunc(w[i]);
         if (q0 == 0) zj[i] = a.Zc[i];
 #pragma unroll
         for (int gi = 0; gi < G; ++gi)
@@ -146,37 +148,45 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
     }
     return;
   }
+  __shared__ float hf[kMaxBasis];                  // OP_CGS3: the coefficients in FP32
+  if (op == OP_CGS3) {
+    for (int p = threadIdx.x; p < k; p += kVecThreads) hf[p] = f64_to_f32_trunc(h[p]);
+    __syncthreads();
+  }
   const int nd = vdots ? k + 1 : 1;
   for (int q0 = 0; q0 < nd; q0 += G) {
     const int cnt = min(G, nd - q0);
-    double acc[G];
+    float accf[G];                                 // V_q.w: FP32 products from the FP32 copy
+    double accw = 0.0;                             // w.w in FP64
 #pragma unroll
-    for (int gi = 0; gi < G; ++gi) acc[gi] = 0.0;
+    for (int gi = 0; gi < G; ++gi) accf[gi] = 0.f;
     for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
       double wi = w[i];
       if (q0 == 0) {
         if (op == OP_CGS3) {
           float c = 0.f;
-          for (int p = 0; p < k; ++p) c = fmaf((float)h[p], a.V32[(size_t)p * vl + i], c);
-          wi -= (double)c;
+          for (int p = 0; p < k; ++p) c = fmaf(hf[p], a.V32[(size_t)p * vl + i], c);
+          wi -= f32_to_f64_bits(c);
           w[i] = wi;
         } else if (update) {
           for (int p = 0; p < k; ++p) wi = fma(-h[p], a.V[(size_t)p * vl + i], wi);
           w[i] = wi;
         }
       }
+      const float wf = f64_to_f32_trunc(wi);
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
         if (gi < cnt) {
           const int p = vdots ? q0 + gi : k;
-          const double v = p < k ? a.V[(size_t)p * vl + i] : wi;
-          acc[gi] = fma(v, wi, acc[gi]);
+          if (p < k) accf[gi] = fmaf(a.V32[(size_t)p * vl + i], wf, accf[gi]);
+          else accw = fma(wi, wi, accw);
         }
       }
     }
 #pragma unroll
     for (int gi = 0; gi < G; ++gi) {
-      double t = acc[gi];
+      const int p = vdots ? q0 + gi : k;
+      double t = p < k ? (double)accf[gi] : accw;
 #pragma unroll
       for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
       if (lane == 0) red[gi][wid] = t;
@@ -247,7 +257,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_basis_kernel(const BInst *_
   for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
     const double v = src[i] * dinv;
     vj[i] = v;
-    vj32[i] = (float)v;
+    vj32[i] = f64_to_f32_trunc(v);
     a.Q[i] = v;
   }
 }

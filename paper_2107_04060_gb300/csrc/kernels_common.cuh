@@ -1,5 +1,7 @@
 // Device helpers shared by the kernels: DoF existence / freedom masks of the structured
-// layout (Dirichlet displacement on the boundary, natural pressure condition).
+// layout (Dirichlet displacement on the boundary, natural pressure condition), and
+// FP64 <-> FP32 conversions in integer arithmetic (on this GPU the hardware conversions
+// issue to the FP64 pipe, at a quarter of its fused multiply-add rate).
 #pragma once
 
 #include <type_traits>
@@ -35,6 +37,35 @@ __device__ __forceinline__ void static_for_impl(F &f, std::integer_sequence<int,
 template <int N, typename F>
 __device__ __forceinline__ void static_for(F &&f) {
   static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// binary64 -> binary32 by truncation of the significand (rounding toward zero), from the two
+// formats' bit layouts: the exponent is rebiased (1023 -> 127) and the top 23 of the 52
+// fraction bits are kept.  Magnitudes below the binary32 normal range give a signed zero;
+// magnitudes of 2^128 and above, infinities and NaNs give a NaN.  Integer instructions only,
+// so the conversion does not occupy the FP64 pipe.
+__device__ __forceinline__ float f64_to_f32_trunc(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  unsigned mag = (((hi << 3) | (lo >> 29)) - ((1023u - 127u) << 23)) & 0x7fffffffu;
+  if (e < 1023u - 126u) mag = 0u;
+  if (e > 1023u + 127u) mag = 0x7fc00000u;
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// binary32 -> binary64, exact for normal numbers, infinities and NaNs (the exponent is rebiased
+// 127 -> 1023 and the 23 fraction bits become the top of the 52); subnormal inputs give a
+// signed zero.  Integer instructions only.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned hi = u & 0x80000000u, lo = 0u;
+  if (e != 0u) {
+    const unsigned ed = e == 0xffu ? 0x7ffu : e + (1023u - 127u);
+    hi |= (ed << 20) | ((u & 0x7fffffu) >> 3);
+    lo = u << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 }  // namespace bmg

@@ -1,7 +1,10 @@
 // Vector kernels of the FGMRES solver (Sec. 5.1): block-partial dot products against a
 // set of basis vectors with a deterministic second-stage reduction, the Gram-Schmidt
 // update, scaling, the solution update x += Z y, and precision conversion.
+#include <atomic>
+
 #include "bmg_internal.h"
+#include "kernels_common.cuh"
 
 namespace bmg {
 
@@ -28,12 +31,12 @@ template int launch_fill<float>(float *, float, size_t, cudaStream_t, const int 
 __global__ void d2f_kernel(const double *x, float *y, size_t n) {
   pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (float)x[i];
+    y[i] = f64_to_f32_trunc(x[i]);
 }
 __global__ void f2d_kernel(const float *x, double *y, size_t n) {
   pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (double)x[i];
+    y[i] = f32_to_f64_bits(x[i]);
 }
 int launch_convert_d2f(const double *x, float *y, size_t n, cudaStream_t st) {
   BMG_CUDA(launch_pdl(d2f_kernel, dim3(152 * 8), dim3(256), 0, st, x, y, n));
@@ -122,63 +125,96 @@ int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n, d
   return BMG_OK;
 }
 
-// First Gram-Schmidt pass from an FP32 copy of the basis: partial[q * nblocks + b] = sum
-// over block b's chunk of V32_q . w (q < k), products and the per-thread sums in FP32 (a
-// thread covers a few dozen elements), the CTA and grid sums in FP64.  The pass only has to
-// remove most of w's component along the basis: the FP64 second pass that follows measures
-// and removes what it left (to FP64 accuracy), and the Hessenberg column is the sum of the
-// two passes' coefficients.
-__global__ void __launch_bounds__(256) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
-                                                     const double *__restrict__ w, size_t n,
-                                                     double *__restrict__ partial) {
+// Grid of a Gram-Schmidt kernel with blockDim (32, ty): the CTAs resident on the whole GPU
+// (one wave), cached per (kernel, ty).
+template <typename Kern>
+static int resident_blocks(Kern kern, int ty, size_t smem, std::atomic<int> *cache) {
+  int b = cache[ty].load(std::memory_order_relaxed);
+  if (b > 0) return b;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * ty, smem) != cudaSuccess)
+    return 0;
+  b = nsm * (per_sm > 0 ? per_sm : 1);
+  cache[ty].store(b, std::memory_order_relaxed);
+  return b;
+}
+
+// First Gram-Schmidt pass from an FP32 copy of the basis: partial[q * gridDim.x + b] = CTA b's
+// share of V32_q . w (q < k), products and per-thread sums in FP32 (a thread covers a few
+// dozen elements), the warp and grid sums in FP64.  The pass only has to remove most of w's
+// component along the basis: the second pass measures and removes what it left, and the
+// Hessenberg column is the sum of the two passes' coefficients.
+//
+// Layout as update_dots32_kernel's: blockDim = (32, TY), lane x of warp y owns elements
+// base + 2x, base + 2x + 1 (8-byte loads of V32, 16-byte loads of w) and the vectors
+// q = y * KQ .. y * KQ + KQ - 1.  w is converted to FP32 once per element (integer
+// truncation, no FP64 pipe work), and the next batch's loads are issued before the current
+// batch's products so that memory latency overlaps the arithmetic.
+template <int KQ>
+__global__ void __launch_bounds__(32 * kMaxUpdTY) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
+                                                      const double *__restrict__ w, size_t n,
+                                                      double *__restrict__ partial) {
   pdl_enter();
-  constexpr int G = 8;
-  __shared__ double red[G][8];
-  // groups of 4 elements per thread (16-byte loads); n and ldv are multiples of 4
-  const size_t n4 = n / 4, chunk = (n4 + gridDim.x - 1) / gridDim.x;
-  const size_t c0 = blockIdx.x * chunk;
-  const size_t c1 = c0 + chunk < n4 ? c0 + chunk : n4;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double2 *w2 = reinterpret_cast<const double2 *>(w);
-  for (int q0 = 0; q0 < k; q0 += G) {
-    const int cnt = (k - q0) < G ? (k - q0) : G;
-    float acc[G];
+  const int x = threadIdx.x, q0 = threadIdx.y * KQ;
+  const size_t stride = (size_t)gridDim.x * 64;
+  float acc[KQ];
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = 0.f;
-    for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-      const double2 wa = w2[2 * i], wb = w2[2 * i + 1];
-      const float x0 = (float)wa.x, x1 = (float)wa.y, x2 = (float)wb.x, x3 = (float)wb.y;
+  for (int j = 0; j < KQ; ++j) acc[j] = 0.f;
+  float2 vn[KQ];
+  double2 wn = make_double2(0.0, 0.0);
+  auto load = [&](size_t base) {
+    const size_t i = base + 2 * x;                 // n is even: i < n covers both elements
+    const bool valid = i < n;
+    if (valid) wn = *reinterpret_cast<const double2 *>(w + i);
 #pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (g < cnt) {
-          const float4 v = reinterpret_cast<const float4 *>(V + (size_t)(q0 + g) * ldv)[i];
-          acc[g] = fmaf(v.x, x0, fmaf(v.y, x1, fmaf(v.z, x2, fmaf(v.w, x3, acc[g]))));
-        }
-    }
+    for (int j = 0; j < KQ; ++j)
+      if (q0 + j < k && valid) vn[j] = *reinterpret_cast<const float2 *>(V + (size_t)(q0 + j) * ldv + i);
+      else vn[j] = make_float2(0.f, 0.f);
+  };
+  size_t base = (size_t)blockIdx.x * 64;
+  if (base < n) load(base);
+  for (; base < n; base += stride) {
+    float2 vc[KQ];
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      double a = (double)acc[g];
+    for (int j = 0; j < KQ; ++j) vc[j] = vn[j];
+    const bool valid = base + 2 * x < n;
+    const float w0 = valid ? f64_to_f32_trunc(wn.x) : 0.f, w1 = valid ? f64_to_f32_trunc(wn.y) : 0.f;
+    if (base + stride < n) load(base + stride);
+#pragma unroll
+    for (int j = 0; j < KQ; ++j) acc[j] = fmaf(vc[j].x, w0, fmaf(vc[j].y, w1, acc[j]));
+  }
+#pragma unroll
+  for (int j = 0; j < KQ; ++j) {
+    if (q0 + j < k) {                              // warp-uniform
+      double a = (double)acc[j];
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
-      if (lane == 0) red[g][wid] = a;
+      if (x == 0) partial[(size_t)(q0 + j) * gridDim.x + blockIdx.x] = a;
     }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      double t = 0.0;
-      for (int u = 0; u < 8; ++u) t += red[threadIdx.x][u];
-      partial[(size_t)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
   }
 }
 
-// out[0..k-1] = V32_q . w (first Gram-Schmidt pass, see dots32_kernel)
+// out[0..k-1] = V32_q . w (first Gram-Schmidt pass, see dots32_kernel); 1 <= k <= kUpdKQ *
+// kMaxUpdTY, n even, partial holds max_blocks * k entries
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
-                  int nblocks, double *out, cudaStream_t st) {
+                  int max_blocks, double *out, cudaStream_t st) {
+  if (k <= 0 || k > kUpdKQ * kMaxUpdTY || (n & 1) || (ldv & 1)) return BMG_ERR_ARG;
+  static std::atomic<int> cache[kMaxUpdTY + 1];
+  const int ty = (k + kUpdKQ - 1) / kUpdKQ;
+  int nb = resident_blocks(dots32_kernel<kUpdKQ>, ty, 0, cache);
+  if (nb <= 0) {
+    set_error("dots32: occupancy query failed");
+    return BMG_ERR_CUDA;
+  }
+  const size_t nbatch = (n + 63) / 64;
+  if ((size_t)nb > nbatch) nb = (int)nbatch;
+  if (nb > max_blocks) nb = max_blocks;
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(dots32_kernel, dim3(nblocks), dim3(256), 0, st, V, ldv, k, w, n, partial));
+  BMG_CUDA(launch_pdl(dots32_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), 0, st, V, ldv, k, w, n, partial));
   BMG_CHECK_LAUNCH("dots32_kernel");
-  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, partial, nblocks, k, out));
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, (const double *)partial, nb, k, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
@@ -273,6 +309,119 @@ int launch_update_dots(double *w, const double *V, size_t ldv, int k, const doub
   return BMG_OK;
 }
 
+// w <- w - sum_q h[q] V_q (FP64 basis, FP64 products: the Hessenberg coefficients must describe
+// exactly what is subtracted), fused with the block-partial products V_q . w_new (q < k) of
+// the second Gram-Schmidt pass, formed in FP32 from the basis values just loaded.  The second
+// pass measures a component of the order of the first pass's FP32 error; its FP32 rounding
+// leaves the new basis vector orthogonal to the old ones to about 1e-7, while the Arnoldi
+// relation stays exact to FP64 rounding.  The FP64 pipe does k fused multiply-adds per element
+// (the FP64 form of the pass does 2k) and V is streamed from HBM once.
+//
+// Layout: blockDim = (32, TY).  Lane x of warp y owns element base + x and the basis vectors
+// q = y * KQ .. y * KQ + KQ - 1: a warp's loads of one vector are one coalesced 256-byte
+// row, each thread holds at most KQ values, and the TY partial updates of an element meet
+// in shared memory.  A warp owns its vectors' products, so no cross-warp reduction is needed.
+// The next batch's loads are issued before the current batch's arithmetic.
+template <int KQ>
+__global__ void __launch_bounds__(32 * kMaxUpdTY) update_dots32_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                             size_t ldv, int k, const double *__restrict__ h,
+                                                             size_t n, double *__restrict__ partial) {
+  pdl_enter();
+  extern __shared__ double upd_smem[];
+  const int TY = blockDim.y, x = threadIdx.x, y = threadIdx.y;
+  double *hs = upd_smem;                       // [k]
+  double *part = hs + k;                       // [TY][32]
+  float *wsh = reinterpret_cast<float *>(part + 32 * TY);   // [32]
+  for (int q = y * 32 + x; q < k; q += 32 * TY) hs[q] = h[q];
+  __syncthreads();
+  const int q0 = y * KQ;
+  const size_t stride = (size_t)gridDim.x * 32;
+  float acc[KQ];
+#pragma unroll
+  for (int j = 0; j < KQ; ++j) acc[j] = 0.f;
+  double vn[KQ];
+  double wn = 0.0;
+  auto load = [&](size_t base) {
+    const size_t i = base + x;
+    const bool valid = i < n;
+    wn = (y == 0 && valid) ? w[i] : 0.0;
+#pragma unroll
+    for (int j = 0; j < KQ; ++j)
+      vn[j] = (q0 + j < k && valid) ? V[(size_t)(q0 + j) * ldv + i] : 0.0;
+  };
+  size_t base = (size_t)blockIdx.x * 32;
+  if (base < n) load(base);
+  for (; base < n; base += stride) {
+    double vc[KQ];
+#pragma unroll
+    for (int j = 0; j < KQ; ++j) vc[j] = vn[j];
+    double p = wn;
+    if (base + stride < n) load(base + stride);
+    const size_t i = base + x;
+    const bool valid = i < n;
+#pragma unroll
+    for (int j = 0; j < KQ; ++j)
+      if (q0 + j < k) p = fma(-hs[q0 + j], vc[j], p);      // warp-uniform
+    float wf;
+    if (TY == 1) {
+      if (valid) w[i] = p;
+      wf = f64_to_f32_trunc(p);
+    } else {
+      part[y * 32 + x] = p;
+      __syncthreads();
+      if (y == 0) {
+        double s = part[x];
+        for (int u = 1; u < TY; ++u) s += part[u * 32 + x];
+        if (valid) w[i] = s;
+        wsh[x] = f64_to_f32_trunc(s);
+      }
+      __syncthreads();
+      wf = wsh[x];
+    }
+#pragma unroll
+    for (int j = 0; j < KQ; ++j) acc[j] = fmaf(f64_to_f32_trunc(vc[j]), wf, acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < KQ; ++j) {
+    const int q = q0 + j;
+    if (q < k) {                                 // warp-uniform
+      double a = (double)acc[j];
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
+      if (x == 0) partial[(size_t)q * gridDim.x + blockIdx.x] = a;
+    }
+  }
+}
+
+static size_t update_dots32_smem(int k, int ty) {
+  return sizeof(double) * ((size_t)k + 32 * (size_t)ty) + sizeof(float) * 32;
+}
+
+// out[0..k-1] = V_q . w_new (FP32 products) after w_new = w - V h (FP64);
+// 1 <= k <= kUpdKQ * kMaxUpdTY.  partial holds max_blocks * k entries.
+int launch_update_dots32(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                         double *partial, int max_blocks, double *out, cudaStream_t st) {
+  if (k <= 0 || k > kUpdKQ * kMaxUpdTY) return BMG_ERR_ARG;
+  static std::atomic<int> cache[kMaxUpdTY + 1];
+  const int ty = (k + kUpdKQ - 1) / kUpdKQ;
+  int nb = resident_blocks(update_dots32_kernel<kUpdKQ>, ty, update_dots32_smem(kUpdKQ * ty, ty), cache);
+  if (nb <= 0) {
+    set_error("update_dots32: occupancy query failed");
+    return BMG_ERR_CUDA;
+  }
+  const size_t nbatch = (n + 31) / 32;
+  if ((size_t)nb > nbatch) nb = (int)nbatch;
+  if (nb > max_blocks) nb = max_blocks;
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
+  BMG_CUDA(launch_pdl(update_dots32_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), update_dots32_smem(k, ty), st,
+                      w, V, ldv, k, h, n, partial));
+  BMG_CHECK_LAUNCH("update_dots32_kernel");
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, (const double *)partial, nb, k, out));
+  BMG_PROF_END(st, 0.0);
+  BMG_CHECK_LAUNCH("reduce_partials_kernel");
+  return BMG_OK;
+}
+
 // v = w / s[0]   (s on the device; s[0] == 0 leaves v = 0)
 __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ v,
                              const double *__restrict__ s, size_t n) {
@@ -308,7 +457,8 @@ __global__ void __launch_bounds__(256) correct32_norm_kernel(double *__restrict_
       c.z = fmaf(hq, v.z, c.z); c.w = fmaf(hq, v.w, c.w);
     }
     double2 wa = w2[2 * i], wb = w2[2 * i + 1];
-    wa.x -= (double)c.x; wa.y -= (double)c.y; wb.x -= (double)c.z; wb.y -= (double)c.w;
+    wa.x -= f32_to_f64_bits(c.x); wa.y -= f32_to_f64_bits(c.y);
+    wb.x -= f32_to_f64_bits(c.z); wb.y -= f32_to_f64_bits(c.w);
     w2[2 * i] = wa;
     w2[2 * i + 1] = wb;
     acc = fma(wa.x, wa.x, fma(wa.y, wa.y, fma(wb.x, wb.x, fma(wb.y, wb.y, acc))));
@@ -345,7 +495,7 @@ __global__ void scale2_kernel(const double *__restrict__ w, double *__restrict__
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double x = w[i] * d;
     v[i] = x;
-    v32[i] = (float)x;
+    v32[i] = f64_to_f32_trunc(x);
   }
 }
 int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st) {

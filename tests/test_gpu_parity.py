@@ -248,3 +248,26 @@ def test_error_codes(bmg):
     b[0:5] = float("nan")
     with pytest.raises(bmg.BmgError, match="non-finite"):
         h.fgmres_solve(b, x)
+
+
+def test_fgmres_long_restart_cycles_agree(bmg):
+    """Long Arnoldi cycles (Sec. 5.1's FGMRES with 150-vector restarts) spread the second
+    Gram-Schmidt pass over up to ten warps per CTA (16 basis vectors each); short ones use one.
+    A weakly damped smoother makes the solve need more than 64 iterations; both restart
+    lengths converge to the same solution, and the longer cycle needs no more iterations."""
+    import torch
+    n = 32
+    s = bmg.assemble(n, 1e4, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.15)
+    b = dev(bmg, n, synthetic.rhs(n, 4))
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = h.fgmres_solve(b, x1, rtol=1e-10, restart=40, maxit=2000)
+    i2 = h.fgmres_solve(b, x2, rtol=1e-10, restart=150, maxit=2000)
+    assert i1["status"] == "converged" and i2["status"] == "converged"
+    assert i2["iters"] > 64, i2
+    assert i2["iters"] <= i1["iters"]
+    r = torch.empty_like(b)
+    for x in (x1, x2):
+        s.residual(b, x, r)
+        assert (torch.linalg.norm(r) / torch.linalg.norm(b)).item() <= 1.01e-10
+    assert (torch.linalg.norm(x1 - x2) / torch.linalg.norm(x2)).item() < 1e-6
