@@ -648,7 +648,7 @@ static int ensure_krylov(bmg_hierarchy *h, int m) {
   BMG_CUDA(cudaMalloc(&h->Z, sizeof(double) * vl * m));
   BMG_CUDA(cudaMalloc(&h->w, sizeof(double) * vl));
   BMG_CUDA(cudaMalloc(&h->r, sizeof(double) * vl));
-  BMG_CUDA(cudaMalloc(&h->partial, sizeof(double) * std::max(kDotBlocks, kUpdMaxBlocks) * (m + 2)));
+  BMG_CUDA(cudaMalloc(&h->partial, sizeof(double) * std::max(kDotBlocks, kGsMaxBlocks) * (m + 2)));
   BMG_CUDA(cudaMalloc(&h->dres, sizeof(double) * 4 * (m + 2)));
   BMG_CUDA(cudaMallocHost(&h->hres, sizeof(double) * 4 * (m + 2)));
   h->m_alloc = m;
@@ -719,12 +719,12 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if ((rc = vcycle_any(h, vj, zj, st))) return rc;
       if ((rc = launch_apply<double>(h->fine_op, zj, nullptr, h->w, false, 1, 0, st))) return rc;
       double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
-      // CGS2: h1 = V^T w (from the FP32 copy of V); w -= V h1 (FP64) fused with h2 = V^T w
-      // (FP32 products); w -= V h2 (the product from the FP32 copy) fused with ||w||^2
-      if ((rc = launch_dots32(h->V32, ldv, j + 1, h->w, vl, h->partial, kUpdMaxBlocks, d1, st))) return rc;
-      if ((rc = launch_update_dots32(h->w, h->V, ldv, j + 1, d1, vl, h->partial, kUpdMaxBlocks, d2, st)))
+      // CGS2: h1 = V^T w (from the FP32 copy of V); w -= V h1 (FP64) fused with h2 = V^T w;
+      // w -= V h2 fused with ||w||^2 (both double-float products on the FP32 pipe)
+      if ((rc = launch_dots32(h->V32, ldv, j + 1, h->w, vl, h->partial, kGsMaxBlocks, d1, st))) return rc;
+      if ((rc = launch_update_dots_df(h->w, h->V, ldv, j + 1, d1, vl, h->partial, kGsMaxBlocks, d2, st)))
         return rc;
-      if ((rc = launch_correct32_norm(h->w, h->V32, ldv, j + 1, d2, vl, h->partial, kDotBlocks, d3, st))) return rc;
+      if ((rc = launch_correct_df_norm(h->w, h->V, ldv, j + 1, d2, vl, h->partial, kDotBlocks, d3, st))) return rc;
       BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
       BMG_CUDA(cudaStreamSynchronize(st));
       const double hn = std::sqrt(hr[2 * (m + 2)]);

@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(kVecThreads) batch_copyout_kernel(const BInst 
 //   OP_NORM_B: b.b                       OP_NORM_R: r.r (gate_end)
 //   OP_CGS1:   V_q.w (q <= j) from the FP32 copy of V (FP32 products and per-thread sums,
 //              FP64 beyond); also Z_j = z (gate_iter)
-//   OP_CGS2:   w -= V d1 (FP64); V_q.w (q <= j) from the FP32 copy of V (FP32 products), w.w
-//   OP_CGS3:   w -= V d2 with the product V d2 from the FP32 copy of V; w.w
+//   OP_CGS2:   w -= V d1 (FP64); V_q.w (q <= j) in double-float arithmetic, w.w
+//   OP_CGS3:   w -= V d2 with the product V d2 in double-float arithmetic; w.w
 // Products are stored at partial[slot][chunk] (slot q for V_q.w, slot j + 1 for w.w; slot 0
 // for a norm), then summed over the chunks in a fixed order by batch_reduce_kernel.
 __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__restrict__ I,
@@ -148,45 +148,59 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
     }
     return;
   }
-  __shared__ float hf[kMaxBasis];                  // OP_CGS3: the coefficients in FP32
+  __shared__ float2 hf[kMaxBasis];                 // OP_CGS3: the coefficients, head and tail
   if (op == OP_CGS3) {
-    for (int p = threadIdx.x; p < k; p += kVecThreads) hf[p] = f64_to_f32_trunc(h[p]);
+    for (int p = threadIdx.x; p < k; p += kVecThreads) {
+      float2 t;
+      split_f64(h[p], t.x, t.y);
+      hf[p] = t;
+    }
     __syncthreads();
   }
   const int nd = vdots ? k + 1 : 1;
   for (int q0 = 0; q0 < nd; q0 += G) {
     const int cnt = min(G, nd - q0);
-    float accf[G];                                 // V_q.w: FP32 products from the FP32 copy
+    float sh[G], sl[G];                            // V_q.w: double-float sums
     double accw = 0.0;                             // w.w in FP64
 #pragma unroll
-    for (int gi = 0; gi < G; ++gi) accf[gi] = 0.f;
+    for (int gi = 0; gi < G; ++gi) sh[gi] = sl[gi] = 0.f;
     for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
       double wi = w[i];
       if (q0 == 0) {
         if (op == OP_CGS3) {
-          float c = 0.f;
-          for (int p = 0; p < k; ++p) c = fmaf(hf[p], a.V32[(size_t)p * vl + i], c);
-          wi -= f32_to_f64_bits(c);
+          float ch = 0.f, cl = 0.f;
+          for (int p = 0; p < k; ++p) {
+            float vh, vt;
+            split_f64(a.V[(size_t)p * vl + i], vh, vt);
+            df_dot_step(hf[p].x, hf[p].y, vh, vt, ch, cl);
+          }
+          wi -= f32_to_f64_bits(ch) + f32_to_f64_bits(cl);
           w[i] = wi;
         } else if (update) {
           for (int p = 0; p < k; ++p) wi = fma(-h[p], a.V[(size_t)p * vl + i], wi);
           w[i] = wi;
         }
       }
-      const float wf = f64_to_f32_trunc(wi);
+      float wh = 0.f, wl = 0.f;
+      if (vdots) split_f64(wi, wh, wl);
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
         if (gi < cnt) {
           const int p = vdots ? q0 + gi : k;
-          if (p < k) accf[gi] = fmaf(a.V32[(size_t)p * vl + i], wf, accf[gi]);
-          else accw = fma(wi, wi, accw);
+          if (p < k) {
+            float vh, vt;
+            split_f64(a.V[(size_t)p * vl + i], vh, vt);
+            df_dot_step(vh, vt, wh, wl, sh[gi], sl[gi]);
+          } else {
+            accw = fma(wi, wi, accw);
+          }
         }
       }
     }
 #pragma unroll
     for (int gi = 0; gi < G; ++gi) {
       const int p = vdots ? q0 + gi : k;
-      double t = p < k ? (double)accf[gi] : accw;
+      double t = p < k ? f32_to_f64_bits(sh[gi]) + f32_to_f64_bits(sl[gi]) : accw;
 #pragma unroll
       for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
       if (lane == 0) red[gi][wid] = t;

@@ -331,21 +331,23 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
                   cudaStream_t st);
 int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                        int dots, double *partial, int nblocks, double *out, cudaStream_t st);
-// update_dots32: kUpdKQ basis vectors per warp, at most kMaxUpdTY warps per CTA, so
-// k <= kUpdKQ * kMaxUpdTY (covers the largest restart length, 200); kUpdMaxBlocks bounds its
-// grid (the partial-sum buffer holds kUpdMaxBlocks * k entries)
-constexpr int kUpdKQ = 16;
-constexpr int kMaxUpdTY = 16;
-constexpr int kUpdMaxBlocks = 152 * 32;
-static_assert(kUpdKQ * kMaxUpdTY >= 200, "update_dots32 must cover restart lengths up to 200");
-int launch_update_dots32(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+// Gram-Schmidt kernels with blockDim (32, TY): one warp per KQ basis vectors, so
+// k <= KQ * MaxTY (covers the largest restart length, kMaxBasisVecs).  kGsMaxBlocks bounds
+// their grids (the partial-sum buffer holds kGsMaxBlocks * k entries).
+constexpr int kMaxBasisVecs = 200;
+constexpr int kDotsKQ = 16, kDotsMaxTY = 13;      // dots32
+constexpr int kUpdKQ = 12, kUpdMaxTY = 17;        // update_dots_df
+constexpr int kGsMaxBlocks = 152 * 32;
+static_assert(kDotsKQ * kDotsMaxTY >= kMaxBasisVecs && kUpdKQ * kUpdMaxTY >= kMaxBasisVecs,
+              "Gram-Schmidt kernels must cover every restart length");
+int launch_update_dots_df(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                          double *partial, int max_blocks, double *out, cudaStream_t st);
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st);
 int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st);
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                   int max_blocks, double *out, cudaStream_t st);
-int launch_correct32_norm(double *w, const float *V32, size_t ldv, int k, const double *h, size_t n,
-                          double *partial, int nblocks, double *out, cudaStream_t st);
+int launch_correct_df_norm(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                           double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_axpy_multi(double *x, const double *Z, size_t ldz, int k, const double *y,
                       size_t n, cudaStream_t st);
 }  // namespace bmg

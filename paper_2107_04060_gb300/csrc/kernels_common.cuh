@@ -68,4 +68,32 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// v = head + tail exactly up to the tail's own FP32 rounding (relative 2^-24 of the tail,
+// 2^-47 of v): head = f64_to_f32_trunc(v), tail = the 29 dropped fraction bits scaled by
+// 2^(e - 1075) (e the biased binary64 exponent), with v's sign.  Tails below 2^-126 (|v|
+// below about 2^-74) are dropped.
+__device__ __forceinline__ void split_f64(double v, float &head, float &tail) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  head = f64_to_f32_trunc(v);
+  const float r = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((e - 948u) << 23));
+  tail = (e > 948u && e < 1151u) ? __uint_as_float(__float_as_uint(r) ^ (hi & 0x80000000u)) : 0.f;
+}
+
+// One step of a double-float dot product: (sh, sl) += (ah + al) (bh + bl), dropping al bl.
+// ah bh is split exactly into its rounded value and error (fused multiply-add), the running
+// head sum takes it through the error-free two-sum (Knuth), and the tail collects both
+// errors and the cross terms.  The _rn intrinsics keep the compiler from contracting or
+// reassociating the steps.
+__device__ __forceinline__ void df_dot_step(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);
+  const float c = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float t = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(pe, c), err));
+}
+
 }  // namespace bmg

@@ -153,7 +153,7 @@ static int resident_blocks(Kern kern, int ty, size_t smem, std::atomic<int> *cac
 // truncation, no FP64 pipe work), and the next batch's loads are issued before the current
 // batch's products so that memory latency overlaps the arithmetic.
 template <int KQ>
-__global__ void __launch_bounds__(32 * kMaxUpdTY) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
+__global__ void __launch_bounds__(32 * kDotsMaxTY) dots32_kernel(const float *__restrict__ V, size_t ldv, int k,
                                                       const double *__restrict__ w, size_t n,
                                                       double *__restrict__ partial) {
   pdl_enter();
@@ -196,14 +196,14 @@ __global__ void __launch_bounds__(32 * kMaxUpdTY) dots32_kernel(const float *__r
   }
 }
 
-// out[0..k-1] = V32_q . w (first Gram-Schmidt pass, see dots32_kernel); 1 <= k <= kUpdKQ *
-// kMaxUpdTY, n even, partial holds max_blocks * k entries
+// out[0..k-1] = V32_q . w (first Gram-Schmidt pass, see dots32_kernel); 1 <= k <= kDotsKQ *
+// kDotsMaxTY, n even, partial holds max_blocks * k entries
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,
                   int max_blocks, double *out, cudaStream_t st) {
-  if (k <= 0 || k > kUpdKQ * kMaxUpdTY || (n & 1) || (ldv & 1)) return BMG_ERR_ARG;
-  static std::atomic<int> cache[kMaxUpdTY + 1];
-  const int ty = (k + kUpdKQ - 1) / kUpdKQ;
-  int nb = resident_blocks(dots32_kernel<kUpdKQ>, ty, 0, cache);
+  if (k <= 0 || k > kDotsKQ * kDotsMaxTY || (n & 1) || (ldv & 1)) return BMG_ERR_ARG;
+  static std::atomic<int> cache[kDotsMaxTY + 1];
+  const int ty = (k + kDotsKQ - 1) / kDotsKQ;
+  int nb = resident_blocks(dots32_kernel<kDotsKQ>, ty, 0, cache);
   if (nb <= 0) {
     set_error("dots32: occupancy query failed");
     return BMG_ERR_CUDA;
@@ -212,7 +212,7 @@ int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, 
   if ((size_t)nb > nbatch) nb = (int)nbatch;
   if (nb > max_blocks) nb = max_blocks;
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(dots32_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), 0, st, V, ldv, k, w, n, partial));
+  BMG_CUDA(launch_pdl(dots32_kernel<kDotsKQ>, dim3(nb), dim3(32, ty), 0, st, V, ldv, k, w, n, partial));
   BMG_CHECK_LAUNCH("dots32_kernel");
   BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, (const double *)partial, nb, k, out));
   BMG_PROF_END(st, 0.0);
@@ -311,11 +311,13 @@ int launch_update_dots(double *w, const double *V, size_t ldv, int k, const doub
 
 // w <- w - sum_q h[q] V_q (FP64 basis, FP64 products: the Hessenberg coefficients must describe
 // exactly what is subtracted), fused with the block-partial products V_q . w_new (q < k) of
-// the second Gram-Schmidt pass, formed in FP32 from the basis values just loaded.  The second
-// pass measures a component of the order of the first pass's FP32 error; its FP32 rounding
-// leaves the new basis vector orthogonal to the old ones to about 1e-7, while the Arnoldi
-// relation stays exact to FP64 rounding.  The FP64 pipe does k fused multiply-adds per element
-// (the FP64 form of the pass does 2k) and V is streamed from HBM once.
+// the second Gram-Schmidt pass.  Those products are formed on the FP32 pipe in double-float
+// arithmetic (each FP64 value split exactly into a truncated FP32 head and an FP32 tail,
+// head products made exact with a fused multiply-add, running sums kept as an unevaluated
+// FP32 pair by the error-free two-sum), accurate to about 2^-46 relative to the sum of the
+// products' magnitudes: the second pass keeps the new basis vector orthogonal to the old ones
+// far below FP32 rounding, while the FP64 pipe does only the update's k fused multiply-adds
+// per element (the FP64 form of the pass does 2k).  V is streamed from HBM once.
 //
 // Layout: blockDim = (32, TY).  Lane x of warp y owns element base + x and the basis vectors
 // q = y * KQ .. y * KQ + KQ - 1: a warp's loads of one vector are one coalesced 256-byte
@@ -323,22 +325,22 @@ int launch_update_dots(double *w, const double *V, size_t ldv, int k, const doub
 // in shared memory.  A warp owns its vectors' products, so no cross-warp reduction is needed.
 // The next batch's loads are issued before the current batch's arithmetic.
 template <int KQ>
-__global__ void __launch_bounds__(32 * kMaxUpdTY) update_dots32_kernel(double *__restrict__ w, const double *__restrict__ V,
-                                                             size_t ldv, int k, const double *__restrict__ h,
-                                                             size_t n, double *__restrict__ partial) {
+__global__ void __launch_bounds__(32 * kUpdMaxTY) update_dots_df_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                                     size_t ldv, int k, const double *__restrict__ h,
+                                                                     size_t n, double *__restrict__ partial) {
   pdl_enter();
   extern __shared__ double upd_smem[];
   const int TY = blockDim.y, x = threadIdx.x, y = threadIdx.y;
   double *hs = upd_smem;                       // [k]
   double *part = hs + k;                       // [TY][32]
-  float *wsh = reinterpret_cast<float *>(part + 32 * TY);   // [32]
+  float2 *wsh = reinterpret_cast<float2 *>(part + 32 * TY);   // [32] head and tail of w_new
   for (int q = y * 32 + x; q < k; q += 32 * TY) hs[q] = h[q];
   __syncthreads();
   const int q0 = y * KQ;
   const size_t stride = (size_t)gridDim.x * 32;
-  float acc[KQ];
+  float sh[KQ], sl[KQ];                          // double-float running sums of V_q . w_new
 #pragma unroll
-  for (int j = 0; j < KQ; ++j) acc[j] = 0.f;
+  for (int j = 0; j < KQ; ++j) sh[j] = sl[j] = 0.f;
   double vn[KQ];
   double wn = 0.0;
   auto load = [&](size_t base) {
@@ -362,10 +364,10 @@ __global__ void __launch_bounds__(32 * kMaxUpdTY) update_dots32_kernel(double *_
 #pragma unroll
     for (int j = 0; j < KQ; ++j)
       if (q0 + j < k) p = fma(-hs[q0 + j], vc[j], p);      // warp-uniform
-    float wf;
+    float2 ws;
     if (TY == 1) {
       if (valid) w[i] = p;
-      wf = f64_to_f32_trunc(p);
+      split_f64(p, ws.x, ws.y);
     } else {
       part[y * 32 + x] = p;
       __syncthreads();
@@ -373,19 +375,27 @@ __global__ void __launch_bounds__(32 * kMaxUpdTY) update_dots32_kernel(double *_
         double s = part[x];
         for (int u = 1; u < TY; ++u) s += part[u * 32 + x];
         if (valid) w[i] = s;
-        wsh[x] = f64_to_f32_trunc(s);
+        float2 t;
+        split_f64(s, t.x, t.y);
+        wsh[x] = t;
       }
       __syncthreads();
-      wf = wsh[x];
+      ws = wsh[x];
     }
 #pragma unroll
-    for (int j = 0; j < KQ; ++j) acc[j] = fmaf(f64_to_f32_trunc(vc[j]), wf, acc[j]);
+    for (int j = 0; j < KQ; ++j) {
+      if (q0 + j < k) {
+        float vh, vl;
+        split_f64(vc[j], vh, vl);
+        df_dot_step(vh, vl, ws.x, ws.y, sh[j], sl[j]);
+      }
+    }
   }
 #pragma unroll
   for (int j = 0; j < KQ; ++j) {
     const int q = q0 + j;
     if (q < k) {                                 // warp-uniform
-      double a = (double)acc[j];
+      double a = f32_to_f64_bits(sh[j]) + f32_to_f64_bits(sl[j]);
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
       if (x == 0) partial[(size_t)q * gridDim.x + blockIdx.x] = a;
@@ -393,29 +403,29 @@ __global__ void __launch_bounds__(32 * kMaxUpdTY) update_dots32_kernel(double *_
   }
 }
 
-static size_t update_dots32_smem(int k, int ty) {
-  return sizeof(double) * ((size_t)k + 32 * (size_t)ty) + sizeof(float) * 32;
+static size_t update_dots_df_smem(int k, int ty) {
+  return sizeof(double) * ((size_t)k + 32 * (size_t)ty) + sizeof(float2) * 32;
 }
 
-// out[0..k-1] = V_q . w_new (FP32 products) after w_new = w - V h (FP64);
-// 1 <= k <= kUpdKQ * kMaxUpdTY.  partial holds max_blocks * k entries.
-int launch_update_dots32(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
-                         double *partial, int max_blocks, double *out, cudaStream_t st) {
-  if (k <= 0 || k > kUpdKQ * kMaxUpdTY) return BMG_ERR_ARG;
-  static std::atomic<int> cache[kMaxUpdTY + 1];
+// out[0..k-1] = V_q . w_new (double-float products) after w_new = w - V h (FP64);
+// 1 <= k <= kUpdKQ * kUpdMaxTY.  partial holds max_blocks * k entries.
+int launch_update_dots_df(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                          double *partial, int max_blocks, double *out, cudaStream_t st) {
+  if (k <= 0 || k > kUpdKQ * kUpdMaxTY) return BMG_ERR_ARG;
+  static std::atomic<int> cache[kUpdMaxTY + 1];
   const int ty = (k + kUpdKQ - 1) / kUpdKQ;
-  int nb = resident_blocks(update_dots32_kernel<kUpdKQ>, ty, update_dots32_smem(kUpdKQ * ty, ty), cache);
+  int nb = resident_blocks(update_dots_df_kernel<kUpdKQ>, ty, update_dots_df_smem(kUpdKQ * ty, ty), cache);
   if (nb <= 0) {
-    set_error("update_dots32: occupancy query failed");
+    set_error("update_dots_df: occupancy query failed");
     return BMG_ERR_CUDA;
   }
   const size_t nbatch = (n + 31) / 32;
   if ((size_t)nb > nbatch) nb = (int)nbatch;
   if (nb > max_blocks) nb = max_blocks;
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(update_dots32_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), update_dots32_smem(k, ty), st,
+  BMG_CUDA(launch_pdl(update_dots_df_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), update_dots_df_smem(k, ty), st,
                       w, V, ldv, k, h, n, partial));
-  BMG_CHECK_LAUNCH("update_dots32_kernel");
+  BMG_CHECK_LAUNCH("update_dots_df_kernel");
   BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, (const double *)partial, nb, k, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
@@ -430,38 +440,45 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = w[i] * d;
 }
-// Last Gram-Schmidt correction: w <- w - V h with the product V h formed in FP32 from the
-// FP32 copy of the basis (h is the second pass's coefficient vector, of the order of the
-// first pass's FP32 error, so the FP32 rounding of V h is far below FP64 rounding of w),
-// fused with the block-partial sums of w.w (FP64).
-__global__ void __launch_bounds__(256) correct32_norm_kernel(double *__restrict__ w, const float *__restrict__ V32,
-                                                             size_t ldv, int k, const double *__restrict__ h,
-                                                             size_t n, double *__restrict__ partial) {
+// Last Gram-Schmidt correction: w <- w - V h (h the second pass's coefficients), with the
+// product V h formed in double-float arithmetic on the FP32 pipe from the FP64 basis (each
+// value split exactly into head and tail, see split_f64 / df_dot_step), fused with the
+// block-partial sums of w.w (FP64).  The product is accurate to about 2^-46 of
+// sum_q |h_q V_q|, so what is subtracted is V h to well below FP64 rounding of w: the
+// Hessenberg column h1 + h2 describes the update exactly, whatever the accuracy of the
+// FP32 first pass that h2 corrects.  Two elements per thread (16-byte loads of V and w).
+__global__ void __launch_bounds__(256) correct_df_norm_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                              size_t ldv, int k, const double *__restrict__ h,
+                                                              size_t n, double *__restrict__ partial) {
   pdl_enter();
-  __shared__ float hs[256];
+  __shared__ float2 hs[kMaxBasisVecs];
   __shared__ double red[8];
-  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = (float)h[q];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    float2 t;
+    split_f64(h[q], t.x, t.y);
+    hs[q] = t;
+  }
   __syncthreads();
-  // groups of 4 elements per thread (16-byte loads); n and ldv are multiples of 4
-  const size_t n4 = n / 4, chunk = (n4 + gridDim.x - 1) / gridDim.x;
-  const size_t c0 = blockIdx.x * chunk;
-  const size_t c1 = c0 + chunk < n4 ? c0 + chunk : n4;
+  const size_t n2 = n / 2;                         // n and ldv are even
   double2 *w2 = reinterpret_cast<double2 *>(w);
   double acc = 0.0;
-  for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
+#pragma unroll 4
     for (int q = 0; q < k; ++q) {
-      const float4 v = reinterpret_cast<const float4 *>(V32 + (size_t)q * ldv)[i];
-      const float hq = hs[q];
-      c.x = fmaf(hq, v.x, c.x); c.y = fmaf(hq, v.y, c.y);
-      c.z = fmaf(hq, v.z, c.z); c.w = fmaf(hq, v.w, c.w);
+      const double2 v = reinterpret_cast<const double2 *>(V + (size_t)q * ldv)[i];
+      const float2 hq = hs[q];
+      float vh, vl;
+      split_f64(v.x, vh, vl);
+      df_dot_step(hq.x, hq.y, vh, vl, ch0, cl0);
+      split_f64(v.y, vh, vl);
+      df_dot_step(hq.x, hq.y, vh, vl, ch1, cl1);
     }
-    double2 wa = w2[2 * i], wb = w2[2 * i + 1];
-    wa.x -= f32_to_f64_bits(c.x); wa.y -= f32_to_f64_bits(c.y);
-    wb.x -= f32_to_f64_bits(c.z); wb.y -= f32_to_f64_bits(c.w);
-    w2[2 * i] = wa;
-    w2[2 * i + 1] = wb;
-    acc = fma(wa.x, wa.x, fma(wa.y, wa.y, fma(wb.x, wb.x, fma(wb.y, wb.y, acc))));
+    double2 wi = w2[i];
+    wi.x -= f32_to_f64_bits(ch0) + f32_to_f64_bits(cl0);
+    wi.y -= f32_to_f64_bits(ch1) + f32_to_f64_bits(cl1);
+    w2[i] = wi;
+    acc = fma(wi.x, wi.x, fma(wi.y, wi.y, acc));
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
@@ -475,12 +492,14 @@ __global__ void __launch_bounds__(256) correct32_norm_kernel(double *__restrict_
   }
 }
 
-// out[0] = ||w_new||^2 after w_new = w - V32 h (see correct32_norm_kernel); k <= 256
-int launch_correct32_norm(double *w, const float *V32, size_t ldv, int k, const double *h, size_t n,
-                          double *partial, int nblocks, double *out, cudaStream_t st) {
+// out[0] = ||w_new||^2 after w_new = w - V h (see correct_df_norm_kernel); 1 <= k <=
+// kMaxBasisVecs, n and ldv even
+int launch_correct_df_norm(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                           double *partial, int nblocks, double *out, cudaStream_t st) {
+  if (k <= 0 || k > kMaxBasisVecs || (n & 1) || (ldv & 1)) return BMG_ERR_ARG;
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(correct32_norm_kernel, dim3(nblocks), dim3(256), 0, st, w, V32, ldv, k, h, n, partial));
-  BMG_CHECK_LAUNCH("correct32_norm_kernel");
+  BMG_CUDA(launch_pdl(correct_df_norm_kernel, dim3(nblocks), dim3(256), 0, st, w, V, ldv, k, h, n, partial));
+  BMG_CHECK_LAUNCH("correct_df_norm_kernel");
   BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(1), dim3(256), 0, st, (const double *)partial, nblocks, 1, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
