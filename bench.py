@@ -44,7 +44,8 @@ MAXIT = 1000
 # 1.20 TFLOP/s with a register FMA loop), HBM from the measured-peaks file of this GPU model
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes per fine-level launch of the FP64 operator inside the sweep, from the ncu
-# capture summarised in profiles/launches_fp64_sweep_512.md (null it when the kernel changes)
+# capture summarised in profiles/apply_fp64_512_sweep_full.md (cell-pair kernel with the
+# reduced halo; null it when the kernel changes)
 APPLY_TRAFFIC_BYTES = 42.8e6
 # algorithmic work per grid cell of the fine-level kernels: the operator counts the nonzero
 # products of the element matrices (156 flops per triangle, two triangles per cell, plus 26

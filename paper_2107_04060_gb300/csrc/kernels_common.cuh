@@ -68,16 +68,19 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// v = head + tail exactly up to the tail's own FP32 rounding (relative 2^-24 of the tail,
-// 2^-47 of v): head = f64_to_f32_trunc(v), tail = the 29 dropped fraction bits scaled by
-// 2^(e - 1075) (e the biased binary64 exponent), with v's sign.  Tails below 2^-126 (|v|
-// below about 2^-74) are dropped.
+// v = head + tail with head = f64_to_f32_trunc(v) and tail the 29 fraction bits that head
+// drops, of which the top 23 are kept (relative error 2^-23 of the tail, 2^-46 of v): those
+// 23 bits become an exact float by the magic-number construction (2^23 + m has m as its
+// fraction field, and subtracting 2^23 is exact), scaled by 2^(e - 1069) (e the biased
+// binary64 exponent) and given v's sign.  Integer and FP32 instructions only (no conversion
+// instruction).  Tails below the FP32 normal range (|v| below about 2^-80) are dropped.
 __device__ __forceinline__ void split_f64(double v, float &head, float &tail) {
   const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
   const unsigned e = (hi >> 20) & 0x7ffu;
   head = f64_to_f32_trunc(v);
-  const float r = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((e - 948u) << 23));
-  tail = (e > 948u && e < 1151u) ? __uint_as_float(__float_as_uint(r) ^ (hi & 0x80000000u)) : 0.f;
+  const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((lo >> 6) & 0x7fffffu)), 8388608.0f);
+  const float r = __fmul_rn(m, __uint_as_float((e - 942u) << 23));
+  tail = (e > 942u && e < 1151u) ? __uint_as_float(__float_as_uint(r) ^ (hi & 0x80000000u)) : 0.f;
 }
 
 // One step of a double-float dot product: (sh, sl) += (ah + al) (bh + bl), dropping al bl.

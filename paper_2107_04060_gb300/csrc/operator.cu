@@ -1,11 +1,13 @@
 // Matrix-free application of the reduced-quadrature Biot operator (Sec. 2.3,
 // Eq. block_form_rq) on the structured triangulation: y = A x or r = b - A x.
 //
-// Element-gather design: a CTA owns a 32 x 8 tile of output positions.  Phase 1 computes
-// the 13-entry local products of both triangles of every cell of the tile plus a one-cell
-// halo on the low side (the triangles that touch the tile's DoFs) into shared memory;
-// phase 2 gathers, for every DoF of the tile, the contributions of its triangles (6 for a
-// vertex, 2 for an edge, 1 for a triangle).  No atomics: the result is deterministic.
+// Element-gather design: a CTA owns a tile of output positions.  Phase 1 computes, one task
+// per cell, the local products of the cell's two triangles into 20 shared-memory slots (the
+// rows of the six DoFs the two triangles share continue one sum), for the tile's cells and
+// for a one-cell halo on the low side, where only the rows the tile's DoFs need are formed;
+// phase 2 gathers, for every DoF of the tile, the slots of the cells around it (4 for a
+// vertex, 2 for an edge off the diagonal, 1 otherwise).  No atomics: the result is
+// deterministic.
 // Constrained displacement slots are ignored on input and written as 0.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -35,49 +37,78 @@ struct ApplyArgs {
 };
 
 
-// Local product of one triangle: yl[13] = E_T xl, xl = (u[9], w[3], p).  Products with the
-// structural zeros of the element matrices are not formed (Aeps 30 of 81, g 2 of 9, the
-// unit RT0 mass 4 of 9; see kElemNonzeros).
-template <typename T, int WM>
+// Local product of one triangle, accumulated: yl[a] += (E_T xl)_a for the rows a in ROWS
+// (bit a; 13 rows), xl = (u[9], w[3], p).  Products with the structural zeros of the
+// element matrices are not formed (Aeps 30 of 81, g 2 of 9, the unit RT0 mass 4 of 9; see
+// kElemNonzeros), and neither are the rows outside ROWS nor the shared terms only they use.
+// Every row is one chain of fused multiply-adds starting from yl[a], so a row that continues
+// another triangle's sum for the same DoF costs no separate addition.
+constexpr unsigned kAllRows = 0x1fffu;
+
+template <unsigned ROWS>
+__host__ __device__ constexpr bool rows_need_gu() {
+  bool need = (ROWS >> 12) & 1u;                   // the pressure row
+  for (int a = 0; a < 9; ++a) need = need || (((ROWS >> a) & 1u) && g_nonzero(a));
+  return need;
+}
+template <unsigned ROWS>
+__host__ __device__ constexpr bool rows_need_s() {
+  bool need = false;
+  for (int a = 0; a < 9; ++a) need = need || (((ROWS >> a) & 1u) && g_nonzero(a));
+  return need;
+}
+
+template <typename T, int WM, unsigned ROWS>
 __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T u[9],
                                             const T w[3], T p, T kinv, const T *wmT,
                                             T *yl) {
-  T gu = 0;
-  static_for<9>([&](auto k_) {
-    constexpr int k = decltype(k_)::value;
-    if constexpr (g_nonzero(k)) gu = fma(c.g[o][k], u[k], gu);
-  });
-  const T s = c.lam_area * gu - c.alpha * p;
+  T gu = 0, s = 0;
+  if constexpr (rows_need_gu<ROWS>()) {
+    static_for<9>([&](auto k_) {
+      constexpr int k = decltype(k_)::value;
+      if constexpr (g_nonzero(k)) gu = fma(c.g[o][k], u[k], gu);
+    });
+  }
+  if constexpr (rows_need_s<ROWS>()) s = fma(c.lam_area, gu, -c.alpha * p);
   static_for<9>([&](auto a_) {
     constexpr int a = decltype(a_)::value;
-    T acc = 0;
-    if constexpr (g_nonzero(a)) acc = c.g[o][a] * s;
-    static_for<9>([&](auto b_) {
-      constexpr int b = decltype(b_)::value;
-      if constexpr (aeps_nonzero(a, b)) acc = fma(c.A[o][a * 9 + b], u[b], acc);
-    });
-    yl[a] = acc;
-  });
-  T dww = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) dww = fma(c.dw[o][k], w[k], dww);
-  if (WM == 0) {
-    static_for<3>([&](auto a_) {
-      constexpr int a = decltype(a_)::value;
-      T acc = 0;
-      static_for<3>([&](auto b_) {
+    if constexpr (((ROWS >> a) & 1u) != 0) {
+      T acc = yl[a];
+      if constexpr (g_nonzero(a)) acc = fma(c.g[o][a], s, acc);
+      static_for<9>([&](auto b_) {
         constexpr int b = decltype(b_)::value;
-        if constexpr (mw_nonzero(a, b)) acc = fma(c.M1[o][a * 3 + b], w[b], acc);
+        if constexpr (aeps_nonzero(a, b)) acc = fma(c.A[o][a * 9 + b], u[b], acc);
       });
-      yl[9 + a] = kinv * acc - c.dw[o][a] * p;
-    });
-  } else {
-    // symmetric 3x3: (00, 01, 02, 11, 12, 22)
-    yl[9] = wmT[0] * w[0] + wmT[1] * w[1] + wmT[2] * w[2] - c.dw[o][0] * p;
-    yl[10] = wmT[1] * w[0] + wmT[3] * w[1] + wmT[4] * w[2] - c.dw[o][1] * p;
-    yl[11] = wmT[2] * w[0] + wmT[4] * w[1] + wmT[5] * w[2] - c.dw[o][2] * p;
+      yl[a] = acc;
+    }
+  });
+  static_for<3>([&](auto a_) {
+    constexpr int a = decltype(a_)::value;
+    if constexpr (((ROWS >> (9 + a)) & 1u) != 0) {
+      T m = 0;
+      if constexpr (WM == 0) {
+        static_for<3>([&](auto b_) {
+          constexpr int b = decltype(b_)::value;
+          if constexpr (mw_nonzero(a, b)) m = fma(c.M1[o][a * 3 + b], w[b], m);
+        });
+        yl[9 + a] = fma(kinv, m, fma(-c.dw[o][a], p, yl[9 + a]));
+      } else {
+        // symmetric 3x3: (00, 01, 02, 11, 12, 22)
+        constexpr int r0 = a == 0 ? 0 : a == 1 ? 1 : 2;
+        constexpr int r1 = a == 0 ? 1 : a == 1 ? 3 : 4;
+        constexpr int r2 = a == 0 ? 2 : a == 1 ? 4 : 5;
+        m = fma(wmT[r0], w[0], fma(wmT[r1], w[1], fma(wmT[r2], w[2], fma(-c.dw[o][a], p, yl[9 + a]))));
+        yl[9 + a] = m;
+      }
+    }
+  });
+  if constexpr (((ROWS >> 12) & 1u) != 0) {
+    T r = fma(-c.pp, p, yl[12]);
+    r = fma(-c.alpha, gu, r);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r = fma(-c.dw[o][k], w[k], r);
+    yl[12] = r;
   }
-  yl[12] = -c.alpha * gu - dww - c.pp * p;
 }
 
 // Where phase 1 reads the input vector and the coefficients: global memory, or a slab of
@@ -113,71 +144,128 @@ struct SmemSrc {                 // slab: x [10][BY][BX], coefficients [NC][BY -
   }
 };
 
+// Both triangles of cell (ci, cj), accumulated into the cell's kCellSlots shared-memory
+// slots.  L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj).
+// U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1).
+// The two triangles share the vertices (ci+1,cj) and (ci,cj+1) and the diagonal edge: U's
+// rows for those six DoFs continue L's sums, so each cell leaves 20 values:
+//   0 ux(ci,cj)  1 uy(ci,cj)  2 bv(ci,cj)  3 bh(ci,cj)  4 wv(ci,cj)  5 wh(ci,cj)  6 pL
+//   7 ux(ci+1,cj)  8 uy(ci+1,cj)  9 ux(ci,cj+1)  10 uy(ci,cj+1)  11 bd  12 wd
+//   13 ux(ci+1,cj+1)  14 uy(ci+1,cj+1)  15 bv(ci+1,cj)  16 bh(ci,cj+1)  17 wv(ci+1,cj)
+//   18 wh(ci,cj+1)  19 pU
+// LROWS / UROWS select the rows of each triangle that are formed (halo cells need a few).
+constexpr int kCellSlots = 20;
+
+template <typename T, int WM, unsigned LROWS, unsigned UROWS, typename Src>
+__device__ __forceinline__ void cell_product(const OpCoefs<T> &c, const Src &src, int ci, int cj, int n,
+                                             T *slot) {
+  if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
+#pragma unroll
+    for (int k = 0; k < kCellSlots; ++k) slot[k] = 0;
+    return;
+  }
+  const bool f00 = vfree(ci, cj, n), f10 = vfree(ci + 1, cj, n), f01 = vfree(ci, cj + 1, n),
+             f11 = vfree(ci + 1, cj + 1, n);
+  const T ux00 = f00 ? src.xv(UX, ci, cj) : T(0), uy00 = f00 ? src.xv(UY, ci, cj) : T(0);
+  const T ux10 = f10 ? src.xv(UX, ci + 1, cj) : T(0), uy10 = f10 ? src.xv(UY, ci + 1, cj) : T(0);
+  const T ux01 = f01 ? src.xv(UX, ci, cj + 1) : T(0), uy01 = f01 ? src.xv(UY, ci, cj + 1) : T(0);
+  const T ux11 = f11 ? src.xv(UX, ci + 1, cj + 1) : T(0), uy11 = f11 ? src.xv(UY, ci + 1, cj + 1) : T(0);
+  const T bd = src.xv(BD, ci, cj);
+  const T bvL = ci > 0 ? src.xv(BV, ci, cj) : T(0), bvU = ci + 1 < n ? src.xv(BV, ci + 1, cj) : T(0);
+  const T bhL = cj > 0 ? src.xv(BH, ci, cj) : T(0), bhU = cj + 1 < n ? src.xv(BH, ci, cj + 1) : T(0);
+  const T wd = src.xv(WD, ci, cj);
+  const T wvL = src.xv(WV, ci, cj), wvU = src.xv(WV, ci + 1, cj);
+  const T whL = src.xv(WH, ci, cj), whU = src.xv(WH, ci, cj + 1);
+  T kin[2] = {0, 0};
+  T wm[2][6];
+  if (WM == 0) {
+    kin[0] = src.kv(0, ci, cj);
+    kin[1] = src.kv(1, ci, cj);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      wm[0][k] = src.wv(0, k, ci, cj);
+      wm[1][k] = src.wv(1, k, ci, cj);
+    }
+  }
+  T yl[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) yl[k] = 0;
+  {
+    const T u[9] = {ux00, ux10, ux01, uy00, uy10, uy01, bd, bvL, bhL};
+    const T w[3] = {wd, wvL, whL};
+    tri_product<T, WM, LROWS>(c, 0, u, w, src.xv(PL, ci, cj), kin[0], wm[0], yl);
+  }
+  slot[0] = yl[0]; slot[1] = yl[3]; slot[2] = yl[7]; slot[3] = yl[8];
+  slot[4] = yl[10]; slot[5] = yl[11]; slot[6] = yl[12];
+  T yu[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) yu[k] = 0;
+  yu[2] = yl[1]; yu[5] = yl[4]; yu[1] = yl[2]; yu[4] = yl[5]; yu[6] = yl[6]; yu[9] = yl[9];
+  {
+    const T u[9] = {ux11, ux01, ux10, uy11, uy01, uy10, bd, bvU, bhU};
+    const T w[3] = {wd, wvU, whU};
+    tri_product<T, WM, UROWS>(c, 1, u, w, src.xv(PU, ci, cj), kin[1], wm[1], yu);
+  }
+  slot[7] = yu[2]; slot[8] = yu[5]; slot[9] = yu[1]; slot[10] = yu[4]; slot[11] = yu[6];
+  slot[12] = yu[9]; slot[13] = yu[0]; slot[14] = yu[3]; slot[15] = yu[7]; slot[16] = yu[8];
+  slot[17] = yu[10]; slot[18] = yu[11]; slot[19] = yu[12];
+}
+
+__host__ __device__ constexpr unsigned rowbits(int a) { return 1u << a; }
+// rows the tile's DoFs gather from its halo cells (see the gather in apply_tile):
+// left column (ci = i0 - 1): slots 7, 8 (L rows 1, 4 + U rows 2, 5), 13, 14 (U 0, 3), 15 (U 7),
+// 17 (U 10); bottom row (cj = j0 - 1): slots 9, 10 (L 2, 5 + U 1, 4), 13, 14, 16 (U 8),
+// 18 (U 11); corner: slots 13, 14
+constexpr unsigned kLeftL = rowbits(1) | rowbits(4);
+constexpr unsigned kLeftU = rowbits(0) | rowbits(2) | rowbits(3) | rowbits(5) | rowbits(7) | rowbits(10);
+constexpr unsigned kBottomL = rowbits(2) | rowbits(5);
+constexpr unsigned kBottomU = rowbits(0) | rowbits(1) | rowbits(3) | rowbits(4) | rowbits(8) | rowbits(11);
+constexpr unsigned kCornerU = rowbits(0) | rowbits(3);
+
+__host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
+
 // Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
 // tiles on the coarse levels so that their work spreads over many SMs).  sy: shared scratch
-// of 26 values per cell of the tile and its halo.
+// of kCellSlots values per cell of the tile and of its one-cell halo on the low side.
 template <typename T, int WM, int kTX, int kTY, int NT, typename Src>
-__device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src, T (*sy)[26], int bx,
+__device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src, T (*sy)[kCellSlots], int bx,
                                            int by, size_t boff) {
-  constexpr int kEX = kTX + 1, kEY = kTY + 1;
-  static_assert(NT >= kTX * kTY, "one thread per output position in phase 2");
+  constexpr int kEX = kTX + 1;
+  constexpr int kOwn = kTX * kTY;
+  static_assert(NT >= kOwn, "one thread per output position in phase 2");
+  // halo tasks: bottom row (kTX cells), left column (kTY cells), corner; each kind starts on
+  // a warp boundary where the CTA has the threads, after the own cells if they leave room
+  constexpr int kH0 = round32(kOwn) + round32(kTX) + kTY + 1 <= NT ? round32(kOwn) : 0;
+  constexpr int kHL = kH0 + round32(kTX) + kTY <= NT ? kH0 + round32(kTX) : kH0 + kTX;
+  constexpr int kHC = kHL + round32(kTY) < NT ? kHL + round32(kTY) : kHL + kTY;
+  static_assert(kHC < NT && kH0 + kTX <= kHL && kHL + kTY <= kHC, "halo task layout");
   const Grid g = a.g;
   const int n = g.n, P = g.pitch;
   const size_t blk = g.blk;
   T *y = a.y + boff;
   const int i0 = bx * kTX, j0 = by * kTY;
   const int tid = threadIdx.x;
+  auto S = [&](int ci, int cj) -> T * { return sy[(cj - j0 + 1) * kEX + (ci - i0 + 1)]; };
 
-  // phase 1: one task per triangle of the tile plus its low-side halo; all lower-left
-  // triangles come first so that a warp works on one orientation (no divergence between
-  // the two inlined element products)
-  constexpr int NE = kEX * kEY;
-  for (int e = tid; e < 2 * NE; e += NT) {
-    const int o = e >= NE ? 1 : 0, cell = e - o * NE;
-    const int ci = i0 - 1 + cell % kEX, cj = j0 - 1 + cell / kEX;
-    T *yl = sy[cell] + 13 * o;
-    if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
-#pragma unroll
-      for (int k = 0; k < 13; ++k) yl[k] = 0;
-      continue;
-    }
-    // L: v0 = (ci,cj), v1 = (ci+1,cj), v2 = (ci,cj+1); e0 = d, e1 = v(ci,cj), e2 = h(ci,cj)
-    // U: v0 = (ci+1,cj+1), v1 = (ci,cj+1), v2 = (ci+1,cj); e0 = d, e1 = v(ci+1,cj), e2 = h(ci,cj+1)
-    const int v0i = ci + o, v0j = cj + o;
-    const int v1i = o ? ci : ci + 1, v1j = o ? cj + 1 : cj;
-    const int v2i = o ? ci + 1 : ci, v2j = o ? cj : cj + 1;
-    const bool f0 = vfree(v0i, v0j, n), f1 = vfree(v1i, v1j, n), f2 = vfree(v2i, v2j, n);
-    const int evi = ci + o;                          // v(ci + o, cj)
-    const int ehj = cj + o;                          // h(ci, cj + o)
-    const bool bvf = o ? (ci + 1 < n) : (ci > 0);
-    const bool bhf = o ? (cj + 1 < n) : (cj > 0);
-    const T u[9] = {f0 ? src.xv(UX, v0i, v0j) : T(0), f1 ? src.xv(UX, v1i, v1j) : T(0), f2 ? src.xv(UX, v2i, v2j) : T(0),
-                    f0 ? src.xv(UY, v0i, v0j) : T(0), f1 ? src.xv(UY, v1i, v1j) : T(0), f2 ? src.xv(UY, v2i, v2j) : T(0),
-                    src.xv(BD, ci, cj), bvf ? src.xv(BV, evi, cj) : T(0), bhf ? src.xv(BH, ci, ehj) : T(0)};
-    const T w[3] = {src.xv(WD, ci, cj), src.xv(WV, evi, cj), src.xv(WH, ci, ehj)};
-    const T p = src.xv(o ? PU : PL, ci, cj);
-    T kin = 0;
-    T wm[6];
-    if (WM == 0) {
-      kin = src.kv(o, ci, cj);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) wm[k] = src.wv(o, k, ci, cj);
-    }
-    // FP32: orientation as a compile-time constant, so the element coefficients become
-    // immediate constant-bank operands (the FP32 pipe would otherwise wait on indexed
-    // constant loads).  FP64: one shared body with the orientation as an index (fewer
-    // registers, more warps; the FP64 pipe is the limit either way).
-    if constexpr (sizeof(T) == 4) {
-      if (o == 0) tri_product<T, WM>(a.c, 0, u, w, p, kin, wm, yl);
-      else tri_product<T, WM>(a.c, 1, u, w, p, kin, wm, yl);
-    } else {
-      tri_product<T, WM>(a.c, o, u, w, p, kin, wm, yl);
-    }
+  // phase 1: one task per cell of the tile (both triangles), then the halo cells with only
+  // the rows the tile gathers
+  if (tid < kOwn) {
+    const int ci = i0 + tid % kTX, cj = j0 + tid / kTX;
+    cell_product<T, WM, kAllRows, kAllRows>(a.c, src, ci, cj, n, S(ci, cj));
+  }
+  if (tid >= kH0 && tid < kH0 + kTX) {
+    const int ci = i0 + (tid - kH0), cj = j0 - 1;
+    cell_product<T, WM, kBottomL, kBottomU>(a.c, src, ci, cj, n, S(ci, cj));
+  } else if (tid >= kHL && tid < kHL + kTY) {
+    const int ci = i0 - 1, cj = j0 + (tid - kHL);
+    cell_product<T, WM, kLeftL, kLeftU>(a.c, src, ci, cj, n, S(ci, cj));
+  } else if (tid == kHC) {
+    cell_product<T, WM, 0u, kCornerU>(a.c, src, i0 - 1, j0 - 1, n, S(i0 - 1, j0 - 1));
   }
   __syncthreads();
 
-  if (tid >= kTX * kTY) return;
+  if (tid >= kOwn) return;
   const int i = i0 + tid % kTX, j = j0 + tid / kTX;
   if (j > n || i >= P) return;
   const size_t o = (size_t)j * P + i;
@@ -186,22 +274,18 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
     for (int k = 0; k < NBLK; ++k) y[k * blk + o] = 0;
     return;
   }
-  auto Y = [&](int ci, int cj, int k) -> T {
-    return sy[(cj - j0 + 1) * kEX + (ci - i0 + 1)][k];
-  };
+  const T *c00 = S(i, j), *c10 = S(i - 1, j), *c01 = S(i, j - 1), *c11 = S(i - 1, j - 1);
   T v[NBLK];
-  v[UX] = Y(i, j, 0) + Y(i - 1, j, 1) + Y(i, j - 1, 2) + Y(i - 1, j - 1, 13) +
-          Y(i, j - 1, 14) + Y(i - 1, j, 15);
-  v[UY] = Y(i, j, 3) + Y(i - 1, j, 4) + Y(i, j - 1, 5) + Y(i - 1, j - 1, 16) +
-          Y(i, j - 1, 17) + Y(i - 1, j, 18);
-  v[BH] = Y(i, j, 8) + Y(i, j - 1, 21);
-  v[BV] = Y(i, j, 7) + Y(i - 1, j, 20);
-  v[BD] = Y(i, j, 6) + Y(i, j, 19);
-  v[WH] = Y(i, j, 11) + Y(i, j - 1, 24);
-  v[WV] = Y(i, j, 10) + Y(i - 1, j, 23);
-  v[WD] = Y(i, j, 9) + Y(i, j, 22);
-  v[PL] = Y(i, j, 12);
-  v[PU] = Y(i, j, 25);
+  v[UX] = c00[0] + c10[7] + c01[9] + c11[13];
+  v[UY] = c00[1] + c10[8] + c01[10] + c11[14];
+  v[BH] = c00[3] + c01[16];
+  v[BV] = c00[2] + c10[15];
+  v[BD] = c00[11];
+  v[WH] = c00[5] + c01[18];
+  v[WV] = c00[4] + c10[17];
+  v[WD] = c00[12];
+  v[PL] = c00[6];
+  v[PU] = c00[19];
   bool m[NBLK];
   dof_masks(i, j, n, m);
   const T *b = a.residual ? a.b + boff : nullptr;
@@ -220,7 +304,7 @@ __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ Apply
   extern __shared__ unsigned char smem_raw[];
   const size_t boff = (size_t)blockIdx.z * a.bstride;
   const GlobalSrc<T> src{a.x + boff, a.kinv, a.wm, a.g.blk, a.g.pitch};
-  apply_tile<T, WM, kTX, kTY, NT>(a, src, reinterpret_cast<T(*)[26]>(smem_raw), blockIdx.x, blockIdx.y, boff);
+  apply_tile<T, WM, kTX, kTY, NT>(a, src, reinterpret_cast<T(*)[kCellSlots]>(smem_raw), blockIdx.x, blockIdx.y, boff);
 }
 
 // Batched form: several instances of one grid size in one launch, blockIdx.z selecting the
@@ -232,7 +316,7 @@ __global__ void __launch_bounds__(NT) apply_batch_kernel(const ApplyArgs<double>
   const ApplyArgs<double> &a = args[blockIdx.z];
   BMG_GATE(a.gate);
   extern __shared__ unsigned char smem_raw[];
-  double(*sy)[26] = reinterpret_cast<double(*)[26]>(smem_raw);
+  double(*sy)[kCellSlots] = reinterpret_cast<double(*)[kCellSlots]>(smem_raw);
   const GlobalSrc<double> src{a.x, a.kinv, a.wm, a.g.blk, a.g.pitch};
   if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
   else apply_tile<double, 0, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
@@ -284,7 +368,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
 template <int WM>
 constexpr size_t tma_smem_bytes() {
   return 128 + sizeof(float) * (10 * kTmaBY * kTmaBX + (WM ? 12 : 2) * (kTmaBY - 1) * kTmaBX +
-                                26 * (kTmaTX + 1) * (kTmaTY + 1));
+                                kCellSlots * (kTmaTX + 1) * (kTmaTY + 1));
 }
 
 template <int WM>
@@ -300,7 +384,7 @@ __global__ void __launch_bounds__(kTmaNT) apply_tma_kernel(const __grid_constant
   unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   float *xs = reinterpret_cast<float *>(base);
   float *cs = xs + 10 * kTmaBY * kTmaBX;
-  float(*sy)[26] = reinterpret_cast<float(*)[26]>(cs + NC * (kTmaBY - 1) * kTmaBX);
+  float(*sy)[kCellSlots] = reinterpret_cast<float(*)[kCellSlots]>(cs + NC * (kTmaBY - 1) * kTmaBX);
   __shared__ alignas(8) unsigned long long bar;
   const int x0 = blockIdx.x * kTmaTX - 4, y0 = blockIdx.y * kTmaTY - 1;
   const uint32_t b = smem_u32(&bar);
@@ -395,7 +479,7 @@ template <typename T, int WM, int TX, int TY, int NT>
 static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   dim3 block(NT);
   dim3 grid((L.g.pitch + TX - 1) / TX, (L.n + 1 + TY - 1) / TY, batch);
-  const size_t smem = sizeof(T) * 26 * (TX + 1) * (TY + 1);
+  const size_t smem = sizeof(T) * kCellSlots * (TX + 1) * (TY + 1);
   if (smem > 48 * 1024) {
     static bool attr = false;
     if (!attr) {
@@ -493,7 +577,7 @@ template <int TX, int TY, int NT>
 static int launch_apply_batch_tile(const void *d_args, int count, int n, cudaStream_t st) {
   const Grid g = grid_of(n);
   dim3 grid((g.pitch + TX - 1) / TX, (n + 1 + TY - 1) / TY, count);
-  const size_t smem = sizeof(double) * 26 * (TX + 1) * (TY + 1);
+  const size_t smem = sizeof(double) * kCellSlots * (TX + 1) * (TY + 1);
   if (smem > 48 * 1024) {
     const int rc = prepare_apply_batch();
     if (rc) return rc;
@@ -508,7 +592,7 @@ int prepare_apply_batch() {
   static bool done = false;
   if (done) return BMG_OK;
   BMG_CUDA(cudaFuncSetAttribute(apply_batch_kernel<32, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * 26 * 33 * 9)));
+                                (int)(sizeof(double) * kCellSlots * 33 * 9)));
   done = true;
   return BMG_OK;
 }
