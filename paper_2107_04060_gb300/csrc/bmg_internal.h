@@ -329,8 +329,6 @@ int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n,
                 double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_update(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                   cudaStream_t st);
-int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
-                       int dots, double *partial, int nblocks, double *out, cudaStream_t st);
 // Gram-Schmidt kernels with blockDim (32, TY): one warp per KQ basis vectors, so
 // k <= KQ * MaxTY (covers the largest restart length, kMaxBasisVecs).  kGsMaxBlocks bounds
 // their grids (the partial-sum buffer holds kGsMaxBlocks * k entries).

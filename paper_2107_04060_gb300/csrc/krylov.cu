@@ -239,76 +239,6 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
   return BMG_OK;
 }
 
-// w <- w - sum_q h[q] V_q, fused with the block-partial products of the new w against the
-// same basis vectors (q < k, when dots != 0) and with itself (always): one pass over V
-// instead of an update pass and a reduction pass.  Each thread owns a contiguous run of
-// elements; the second loop over the basis re-reads values this thread has just loaded
-// (L1-resident), so V is streamed from HBM once.
-__global__ void __launch_bounds__(256) update_dots_kernel(double *__restrict__ w, const double *__restrict__ V,
-                                                          size_t ldv, int k, const double *__restrict__ h,
-                                                          size_t n, int dots, double *__restrict__ partial) {
-  pdl_enter();
-  constexpr int G = 8;
-  __shared__ double red[G][8];
-  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const size_t c0 = blockIdx.x * chunk;
-  const size_t c1 = c0 + chunk < n ? c0 + chunk : n;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nd = dots ? k + 1 : 1;               // products to form: V_q.w (q < k) and w.w
-  for (int q0 = 0; q0 < nd; q0 += G) {
-    const int cnt = (nd - q0) < G ? (nd - q0) : G;
-    double acc[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = 0.0;
-    for (size_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-      double wi;
-      if (q0 == 0) {                              // first group: form and store the new w
-        wi = w[i];
-        for (int q = 0; q < k; ++q) wi = fma(-h[q], V[(size_t)q * ldv + i], wi);
-        w[i] = wi;
-      } else {
-        wi = w[i];
-      }
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        if (g < cnt) {
-          const int q = dots ? q0 + g : k;
-          const double v = (q < k) ? V[(size_t)q * ldv + i] : wi;
-          acc[g] = fma(v, wi, acc[g]);
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      double a = acc[g];
-#pragma unroll
-      for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
-      if (lane == 0) red[g][wid] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      double t = 0.0;
-      for (int u = 0; u < 8; ++u) t += red[threadIdx.x][u];
-      partial[(size_t)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
-  }
-}
-
-// out[0..k-1] = V_q . w_new, out[k] = w_new . w_new after w_new = w - V h (dots != 0);
-// out[0] = w_new . w_new when dots == 0.
-int launch_update_dots(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
-                       int dots, double *partial, int nblocks, double *out, cudaStream_t st) {
-  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(update_dots_kernel, dim3(nblocks), dim3(256), 0, st, w, V, ldv, k, h, n, dots, partial));
-  BMG_CHECK_LAUNCH("update_dots_kernel");
-  const int cnt = dots ? k + 1 : 1;
-  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(cnt), dim3(256), 0, st, partial, nblocks, cnt, out));
-  BMG_PROF_END(st, 0.0);
-  BMG_CHECK_LAUNCH("reduce_partials_kernel");
-  return BMG_OK;
-}
-
 // w <- w - sum_q h[q] V_q (FP64 basis, FP64 products: the Hessenberg coefficients must describe
 // exactly what is subtracted), fused with the block-partial products V_q . w_new (q < k) of
 // the second Gram-Schmidt pass.  Those products are formed on the FP32 pipe in double-float
