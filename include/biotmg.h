@@ -296,7 +296,7 @@ int bmg_hierarchy_levels(const bmg_hierarchy *h);
  * bmg_hierarchy_tile -- tile chosen at setup (by timing the candidates on this device) for
  * the operator (BMG_PROF_APPLY), Vanka (BMG_PROF_VANKA) or displacement-Vanka
  * (BMG_PROF_VANKA_U) launches of level `level` (0 = finest): 0 = 32 x 8, 1 = 16 x 8,
- * 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 output positions (Vanka: patches; Vanka FP64 has no 0),
+ * 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 output positions (Vanka: patches),
  * 5 = FP32 operator, 32 x 8 with its input staged in shared memory by TMA bulk tensor
  * copies.  -1: not tuned or no such level.  The choice does not change any result.  Setting
  * the environment variable BMG_FORCE_APPLY_TILE to one of these indices before

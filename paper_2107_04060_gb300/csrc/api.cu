@@ -398,7 +398,7 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
     if (rc) return rc;
   }
   if (h->opts.smoother == BMG_VANKA)
-    return pick_tile(&L.tile_vanka, sizeof(T) == 4 ? 0 : 1, 4,
+    return pick_tile(&L.tile_vanka, 0, 4,
                      [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
   return pick_tile(&L.tile_vanka_u, 0, 4,
                    [&] { return launch_bsr_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);

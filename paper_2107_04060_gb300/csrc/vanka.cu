@@ -359,9 +359,12 @@ struct VankaSweepArgs {
 template <typename T, int kPX, int kPY, int NT, bool kKlein = true>
 __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, int by) {
   constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
-  __shared__ T sr[NP * LD];
-  __shared__ T sx[NP * LD];
-  __shared__ int ss[NP];
+  // dynamic shared memory (vanka_smem_bytes): residuals sr[NP][LD], corrections sx[NP][LD],
+  // inverse slots ss[NP]
+  extern __shared__ __align__(16) unsigned char vanka_smem[];
+  T *sr = reinterpret_cast<T *>(vanka_smem);
+  T *sx = sr + NP * LD;
+  int *ss = reinterpret_cast<int *>(sx + NP * LD);
   __shared__ int s_mixed;                          // some patch of the tile has its own inverse
   if (threadIdx.x == 0) s_mixed = 0;
   __syncthreads();
@@ -554,11 +557,24 @@ __global__ void __launch_bounds__(NT) vanka_batch_kernel(const VankaSweepArgs<do
   vanka_tile<double, kPX, kPY, NT, false>(a, blockIdx.x, blockIdx.y);
 }
 
+template <typename T, int PX, int PY>
+constexpr size_t vanka_smem_bytes() {
+  return 2 * (size_t)PX * PY * 21 * sizeof(T) + (size_t)PX * PY * sizeof(int);
+}
+
 template <typename T, int PX, int PY, int NT>
 static void launch_vanka_tile(const VankaSweepArgs<T> &a, const Level &L, cudaStream_t st) {
-  static_assert(2 * PX * PY * 21 * sizeof(T) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
+  constexpr size_t smem = vanka_smem_bytes<T, PX, PY>();
+  static_assert(smem <= 200 * 1024, "shared memory of a Vanka tile");
+  if constexpr (smem > 48 * 1024) {
+    static const bool opted_in = [] {          // once per instantiation, thread-safe
+      return cudaFuncSetAttribute(vanka_sweep_kernel<T, PX, PY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem) == cudaSuccess;
+    }();
+    (void)opted_in;
+  }
   dim3 grid((L.g.pitch + PX - 2) / (PX - 1), (L.n + 1 + PY - 2) / (PY - 1));
-  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT>, dim3(grid), dim3(NT), 0, st, a);
+  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT>, dim3(grid), dim3(NT), smem, st, a);
 }
 
 static long long vanka_ctas(const Level &L, int px, int py) {
@@ -583,15 +599,12 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
   // the largest patch tile that still gives every SM about two CTAs; smaller tiles also
   // spread each patch's rows over more threads
-  // (two 21-wide shared arrays per patch: 32 x 8 patches fit the 48 KB static limit in FP32 only)
+  // (two 21-wide shared arrays per patch: 32 x 8 patches take 43 KB in FP32, 87 KB in FP64)
   const long long want = 2 * 152;
   bool done = true;
-  // tuned at setup: 0 = 32 x 8 (FP32 only), 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 patches
+  // tuned at setup: 0 = 32 x 8, 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 patches
   switch (L.tile_vanka) {
-    case 0:
-      if constexpr (sizeof(T) == 4) launch_vanka_tile<T, 32, 8, 256>(a, L, st);
-      else launch_vanka_tile<T, 16, 8, 256>(a, L, st);
-      break;
+    case 0: launch_vanka_tile<T, 32, 8, 256>(a, L, st); break;
     case 1: launch_vanka_tile<T, 16, 8, 256>(a, L, st); break;
     case 2: launch_vanka_tile<T, 8, 8, 256>(a, L, st); break;
     case 3: launch_vanka_tile<T, 8, 4, 160>(a, L, st); break;
@@ -636,10 +649,11 @@ void make_vanka_args(const Level &L, const double *r, double *x, double omega, b
 
 template <int PX, int PY, int NT>
 static int launch_vanka_batch_tile(const void *d_args, int count, int n, cudaStream_t st) {
-  static_assert(2 * PX * PY * 21 * sizeof(double) + PX * PY * sizeof(int) <= 48 * 1024, "static smem");
+  constexpr size_t smem = vanka_smem_bytes<double, PX, PY>();
+  static_assert(smem <= 48 * 1024, "batched tiles stay within the default shared memory");
   const Grid g = grid_of(n);
   dim3 grid((g.pitch + PX - 2) / (PX - 1), (n + 1 + PY - 2) / (PY - 1), count);
-  vanka_batch_kernel<PX, PY, NT><<<grid, NT, 0, st>>>((const VankaSweepArgs<double> *)d_args);
+  vanka_batch_kernel<PX, PY, NT><<<grid, NT, smem, st>>>((const VankaSweepArgs<double> *)d_args);
   BMG_CHECK_LAUNCH("vanka_batch_kernel");
   return BMG_OK;
 }
