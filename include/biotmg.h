@@ -170,13 +170,13 @@ typedef struct {
 /*
  * bmg_fgmres_solve -- x ~= A^{-1} b by right-preconditioned flexible GMRES(m) with one
  * V-cycle of h as the preconditioner (Sec. 5.1).  Arnoldi by classical Gram-Schmidt with
- * one re-orthogonalisation pass: the first pass's coefficients and the last correction's
- * product V h2 (h2 is of the order of the first pass's FP32 error) come from an FP32 copy of
- * the basis; the second pass's coefficients and the vector updates are FP64 (the Hessenberg
- * column is the sum of both passes).  b, x: device vectors.  The
- * call returns
- * after the solve has finished (it synchronises `stream` once per iteration to read the
- * Hessenberg column).  info may be NULL.
+ * one re-orthogonalisation pass: the first pass's coefficients come from an FP32 copy of the
+ * basis, the update w -= V h1 is FP64, and the second pass's coefficients h2 and the last
+ * correction w -= V h2 are formed in double-float arithmetic (pairs of FP32 values, about
+ * 2^-46 relative) from the FP64 basis; the Hessenberg column is h1 + h2, which describes the
+ * subtracted combination to FP64 rounding.  b, x: device vectors.  The call returns after the
+ * solve has finished (it synchronises `stream` once per iteration to read the Hessenberg
+ * column).  info may be NULL.
  */
 int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
                      const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
@@ -223,9 +223,10 @@ int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
 /*
  * bmg_fgmres_solve_noalloc -- the FGMRES solve of bmg_fgmres_solve (same V-cycle, same
- * CGS2 Arnoldi, except that its first Gram-Schmidt pass runs in FP64 where bmg_fgmres_solve
- * takes it from an FP32 copy of the basis: iteration counts agree within one and both meet
- * the tolerance) for callers that cannot allocate device memory while they run: code that
+ * CGS2 Arnoldi, except that both Gram-Schmidt passes and updates run in FP64, where
+ * bmg_fgmres_solve takes the first pass from an FP32 copy of the basis and forms the second in
+ * double-float arithmetic: iteration counts agree within one and both meet the tolerance)
+ * for callers that cannot allocate device memory while they run: code that
  * works inside a fixed memory budget or a framework that owns every device allocation, or
  * that calls in from a context where cudaMalloc is not allowed.  bmg_fgmres_solve allocates
  * its Krylov workspace with cudaMalloc on its first call (and again when `restart` grows);
