@@ -147,7 +147,7 @@ static int resident_blocks(Kern kern, int ty, size_t smem, std::atomic<int> *cac
 // component along the basis: the second pass measures and removes what it left, and the
 // Hessenberg column is the sum of the two passes' coefficients.
 //
-// Layout as update_dots32_kernel's: blockDim = (32, TY), lane x of warp y owns elements
+// Layout as update_dots_df_kernel's: blockDim = (32, TY), lane x of warp y owns elements
 // base + 2x, base + 2x + 1 (8-byte loads of V32, 16-byte loads of w) and the vectors
 // q = y * KQ .. y * KQ + KQ - 1.  w is converted to FP32 once per element (integer
 // truncation, no FP64 pipe work), and the next batch's loads are issued before the current
