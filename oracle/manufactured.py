@@ -6,9 +6,11 @@ rho_f g = 0 and, for the single backward-Euler step from the exact state, the P0
 (1/M) p, i.e. the right-hand side row of a triangle is -(1/M)|T|.  The pressure condition
 is natural: p = 1 on the boundary enters the RT0 rows as -tau <p, psi . n_out>.
 
-Load integrals use Radon's 7-point degree-5 rule on each triangle.  Parity unpinned as a
-function of its own; it is checked through the convergence rates the paper states (first
-order for |u|_H1, second order for ||p||_L2, Sec. 5.1) in tests/test_oracle_discretization.py.
+Load integrals use Radon's 7-point degree-5 rule on each triangle.  Pinned by
+tests/test_oracle_manufactured.py (the exact field against symbolic derivatives of phi, its
+divergence and boundary values, the rule's exactness to degree 5, the load vector's P0 and
+boundary rows) and through the convergence rates the paper states (first order for |u|_H1,
+second order for ||p||_L2, Sec. 5.1) in tests/test_oracle_mg.py.
 """
 from __future__ import annotations
 
