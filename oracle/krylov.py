@@ -11,7 +11,8 @@ x = x_0 + Z_m y_m.  The iteration stops once the estimate is below rtol ||b||; t
 residual ||b - A x|| / ||b|| is then checked and the method restarts from x if needed.
 Norms are Euclidean over the free DoFs (constrained slots are zero).
 
-Pinned by: direct-solve parity on tiny grids (tests/test_oracle_krylov.py).
+Pinned by: direct-solve parity on tiny grids and a one-iteration solve with the exact
+preconditioner (tests/test_oracle_mg.py).
 """
 from __future__ import annotations
 

@@ -12,6 +12,10 @@ DoFs (Sec. 2.1, Sec. 2.3): P1 displacement (2 per vertex), one face-normal bubbl
 one RT0 flux per edge, one P0 pressure per triangle -- 10 DoF types per cell (Sec. 4.2).
 The oracle numbers DoFs type by type in the order of ``synthetic.TYPES``; inside a type
 row-major over ``[j, i]`` with the shapes of ``synthetic.shapes``.
+
+Pinned by: tests/test_oracle_mesh.py (the triangles tile the square, edge incidence, local
+vertex k opposite local edge k, DoF and Dirichlet counts, patch sizes) and, through the
+assembled matrices, the App. A stencil pins of tests/test_oracle_assembly.py.
 """
 from __future__ import annotations
 

@@ -11,7 +11,7 @@ One V(nu1, nu2) cycle for A_l x = b_l from x = 0:
     level); x <- x + P x_c; nu2 relaxations.
 
 Pinned by: Table 2 / Table 3 two-grid factors and Table 4 iteration counts
-(tests/test_oracle_mg.py); direct-solve parity through FGMRES (tests/test_oracle_krylov.py).
+(tests/test_oracle_mg.py); direct-solve parity through FGMRES (tests/test_oracle_mg.py).
 """
 from __future__ import annotations
 
