@@ -57,3 +57,21 @@ def test_single_rank_needs_no_collective():
     import bench
     assert bench.shard_instances(5, 0, 1) == [0, 1, 2, 3, 4]
     assert bench.max_over_ranks(2.5, 1) == 2.5
+
+
+def test_clock_samples_summary():
+    """The clocks record of the bench line: median SM clock under load, the maximum, and the
+    throttle reasons seen active in any sample (malformed samples are skipped)."""
+    import bench
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1995, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+        "0, 1800, 2070, 1400.0, 0x40, Not Active, Active, Not Active, Not Active",
+    ]
+    s = bench.summarize_clocks(lines)
+    assert s["samples"] == 4 and s["sm_max_mhz"] == 2070.0
+    assert s["sm_mhz"] == (1995.0 + 2070.0) / 2                  # median of 4 samples
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.summarize_clocks([])["samples"] == 0
