@@ -248,7 +248,10 @@ def apply_rows(mesh: Mesh, prm: Params, kinv_L: np.ndarray, kinv_U: np.ndarray, 
                rows) -> np.ndarray:
     """(A x)[rows] computed one row at a time by summing the element contributions of the
     triangles that hold each row's DoF (for sampled checks on grids too large to assemble).
-    Constrained rows return 0 and constrained entries of x are ignored."""
+    Constrained rows return 0 and constrained entries of x are ignored.
+
+    Pinned by: equality with the assembled operator on every row of an 8-cell grid
+    (lognormal K, three parameter sets; tests/test_oracle_assembly.py)."""
     n = mesh.n
     tris = reference_triangles(n)
     parts = {o: element_parts(tris[o]) for o in ("L", "U")}

@@ -18,7 +18,9 @@ with y = (u, w):
     x    <- x + omega (dy, dp)
 The inner Vanka is undamped with natural weights.
 
-Pinned by: the measured two-grid factors of Tables 2 and 3 (tests/test_oracle_mg.py).
+Pinned by: the measured two-grid factors of Tables 2 and 3 (tests/test_oracle_mg.py); the
+patch regularisation for 1/M = 0 by the identity "shifted patches at 1/M = 0 equal the
+unshifted patches at 1/M = s" (tests/test_oracle_mg.py).
 """
 from __future__ import annotations
 
@@ -35,8 +37,14 @@ class Vanka:
     def __init__(self, A: sp.csr_matrix, mesh: Mesh, omega: float, with_flow: bool = True,
                  p_shift: float = 0.0):
         """``with_flow=False`` gives the 8-DoF displacement patches (A must then be the
-        displacement block in the global numbering).  ``p_shift`` is added to the P0
-        diagonal entries of every patch matrix (the regularisation used when 1/M = 0)."""
+        displacement block in the global numbering).
+
+        ``p_shift`` = s >= 0 regularises the patches when 1/M = 0 (Sec. 5.3: a small weight
+        on the diagonal of the Vanka blocks).  Reading: the weight multiplies the pressure
+        mass with the sign of the -(1/M) M_p block, i.e. -s |T| is added to every P0
+        diagonal entry of every patch matrix.  With this reading the shifted patch matrices
+        of a system with 1/M = 0 are exactly the unshifted patch matrices of the same
+        system with 1/M = s (pinned in tests/test_oracle_mg.py)."""
         self.omega = float(omega)
         n = mesh.n
         patches = [mesh.vertex_patch(i, j, with_flow) for j in range(n + 1) for i in range(n + 1)]
@@ -59,7 +67,8 @@ class Vanka:
             cols = np.repeat(idx[:, None, :], s, axis=1)
             mats = np.asarray(A[rows.ravel(), cols.ravel()]).reshape(len(plist), s, s)
             if p_shift != 0.0:
-                mats[:, np.arange(s), np.arange(s)] += p_shift * pmask[idx]
+                area = 0.5 * mesh.h * mesh.h
+                mats[:, np.arange(s), np.arange(s)] -= p_shift * area * pmask[idx]
             inv = np.linalg.inv(mats)
             self.groups.append((idx, inv))
 

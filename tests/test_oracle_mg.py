@@ -145,3 +145,30 @@ def test_galerkin_coarse_rt0_mass_matches_rediscretisation_for_constant_k():
     c = H.levels[1]
     direct = fem.assemble(c.mesh, prm, np.full((8, 8), 2.5), np.full((8, 8), 2.5))
     assert abs(c.A - direct).max() < 1e-12 * abs(direct).max()
+
+
+def test_patch_shift_equals_compressibility():
+    """Sec. 5.3 regularisation (1/M = 0): Vanka patch matrices of the system with 1/M = 0,
+    shifted by p_shift = s, are exactly the patch matrices of the system with 1/M = s
+    (reading: the shift is -s |T| on each P0 diagonal entry, the sign and scale of the
+    -(1/M) M_p block).  Without the shift an interior patch is singular: constant pressure
+    on the patch lies in the null space of its divergence rows."""
+    from oracle.smoothers import Vanka
+    n, s = 8, 1e-3
+    m = Mesh(n)
+    KL, KU = synthetic.lognormal_k(n, 1.0, 3)
+    kl, ku = fem.kinv_from_k(KL, KU)
+    base = dict(lam=1e4, mu=1.0, tau=1.0, alpha=1.0)
+    A0 = fem.assemble(m, fem.Params(inv_M=0.0, **base), kl, ku)
+    As = fem.assemble(m, fem.Params(inv_M=s, **base), kl, ku)
+    v_shift = Vanka(A0, m, 1.0, p_shift=s)
+    v_comp = Vanka(As, m, 1.0)
+    assert len(v_shift.groups) == len(v_comp.groups)
+    for (i1, inv1), (i2, inv2) in zip(v_shift.groups, v_comp.groups):
+        assert np.array_equal(i1, i2)
+        assert np.allclose(inv1, inv2, rtol=1e-12, atol=0.0)
+    # unshifted interior patch at 1/M = 0: singular to working precision
+    p = m.vertex_patch(4, 4)
+    P = A0[p][:, p].toarray()
+    assert np.linalg.cond(P) > 1e12
+    assert np.linalg.cond(P - s * 0.5 * m.h ** 2 * np.diag(fem.type_mask(m, fem.P_TYPES)[p])) < 1e10
