@@ -151,11 +151,16 @@ int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, void *stream,
  */
 int bmg_vcycle(bmg_hierarchy *h, const double *r, double *z, void *stream);
 
+#define BMG_ARNOLDI_FP64 0   /* both Gram-Schmidt passes and updates in FP64 (default)    */
+#define BMG_ARNOLDI_MIXED 1  /* first pass from an FP32 copy of the basis, second pass and
+                                last correction in double-float arithmetic (see below)  */
+
 typedef struct {
   double rtol;      /* stop when ||b - A x|| <= rtol ||b|| (true residual), e.g. 1e-8  */
   int restart;      /* FGMRES restart length m (1..200)                                */
   int maxit;        /* total iteration limit                                           */
   int x0_is_zero;   /* 1: ignore the contents of x on entry; 0: use x as initial guess */
+  int arnoldi;      /* BMG_ARNOLDI_FP64 (0) or BMG_ARNOLDI_MIXED                        */
 } bmg_krylov_opts;
 
 typedef struct {
@@ -170,13 +175,15 @@ typedef struct {
 /*
  * bmg_fgmres_solve -- x ~= A^{-1} b by right-preconditioned flexible GMRES(m) with one
  * V-cycle of h as the preconditioner (Sec. 5.1).  Arnoldi by classical Gram-Schmidt with
- * one re-orthogonalisation pass: the first pass's coefficients come from an FP32 copy of the
+ * one re-orthogonalisation pass (CGS2): h1 = V^T w, w -= V h1, h2 = V^T w, w -= V h2, and the
+ * Hessenberg column is h1 + h2.  With o->arnoldi = BMG_ARNOLDI_FP64 every product and update
+ * is FP64.  With BMG_ARNOLDI_MIXED the first pass's coefficients come from an FP32 copy of the
  * basis, the update w -= V h1 is FP64, and the second pass's coefficients h2 and the last
  * correction w -= V h2 are formed in double-float arithmetic (pairs of FP32 values, about
- * 2^-46 relative) from the FP64 basis; the Hessenberg column is h1 + h2, which describes the
- * subtracted combination to FP64 rounding.  b, x: device vectors.  The call returns after the
- * solve has finished (it synchronises `stream` once per iteration to read the Hessenberg
- * column).  info may be NULL.
+ * 2^-46 relative) from the FP64 basis, which describes the subtracted combination to FP64
+ * rounding; it moves most Gram-Schmidt work from the FP64 pipe to the FP32 pipe.  b, x:
+ * device vectors.  The call returns after the solve has finished (it synchronises `stream`
+ * once per iteration to read the Hessenberg column).  info may be NULL.
  */
 int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
                      const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
@@ -222,10 +229,12 @@ long long bmg_launch_count(void);
 int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
 /*
- * bmg_fgmres_solve_noalloc -- the FGMRES solve of bmg_fgmres_solve (same V-cycle, same
- * CGS2 Arnoldi, except that both Gram-Schmidt passes and updates run in FP64, where
- * bmg_fgmres_solve takes the first pass from an FP32 copy of the basis and forms the second in
- * double-float arithmetic: iteration counts agree within one and both meet the tolerance)
+ * bmg_fgmres_solve_noalloc -- the FGMRES solve of bmg_fgmres_solve with the FP64 Arnoldi
+ * (same V-cycle, same CGS2 in FP64, o->arnoldi is ignored; the Gram-Schmidt passes run as
+ * separate product and update kernels, so the rounding differs from bmg_fgmres_solve's fused
+ * kernels: iteration counts agree within one for lambda/mu <= 1e4 and can differ by a
+ * restart cycle's last few iterations at lambda/mu = 1e6, where the true residual near 1e-8
+ * depends on rounding; both meet the tolerance)
  * for callers that cannot allocate device memory while they run: code that
  * works inside a fixed memory budget or a framework that owns every device allocation, or
  * that calls in from a context where cudaMalloc is not allowed.  bmg_fgmres_solve allocates
@@ -242,7 +251,8 @@ int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
  *   every part of it before reading it.  Calls that overlap on the GPU (different streams or
  *   threads at the same time) race on the array: serialise them.
  *   h, b, x, o, info, stream: as for bmg_fgmres_solve (h is set up beforehand by
- *   bmg_setup_hierarchy, which does allocate).
+ *   bmg_setup_hierarchy, which does allocate).  A bulk-copy wait of the FP32 operator that
+ *   timed out during the solve is reported as BMG_ERR_CUDA, as by bmg_fgmres_solve.
  */
 int bmg_fgmres_solve_noalloc(bmg_hierarchy *h, const double *b, double *x,
                              const bmg_krylov_opts *o, bmg_solve_info *info, void *stream);
@@ -259,11 +269,12 @@ size_t bmg_noalloc_capacity(void);
  *     precision BMG_FP64, nu1 >= 1 and the same nu1, nu2 and n_coarse (omega may differ).
  *     The batch borrows their level data and work vectors: keep them alive, and do not use
  *     them in other solves while a batch solve runs.  1 <= count <= 4096.
- *   o: rtol, restart, maxit and x0_is_zero for every instance (as for bmg_fgmres_solve).
+ *   o: rtol, restart, maxit, x0_is_zero and arnoldi for every instance (as for
+ *     bmg_fgmres_solve).
  *   autotune != 0: time every candidate tile of the batched operator and Vanka kernels on
  *     this batch (per level size) and keep the fastest; 0: the single-instance rule.
- *   Allocates the Krylov workspace of every instance ((2m + 5) FP64 vectors of its size and
- *   an FP32 copy of its m + 1 basis vectors) and
+ *   Allocates the Krylov workspace of every instance ((2m + 5) FP64 vectors of its size, and
+ *   with BMG_ARNOLDI_MIXED an FP32 copy of its m + 1 basis vectors) and
  *   records the solve as one CUDA graph: a prologue (copy-in, ||b||), a device-side while
  *   loop whose body closes cycles and takes one Arnoldi step for every open instance, and
  *   an epilogue (copy-out).  Returns BMG_ERR_ARG on an invalid batch (message names why).
@@ -301,7 +312,10 @@ int bmg_hierarchy_levels(const bmg_hierarchy *h);
  * 5 = FP32 operator, 32 x 8 with its input staged in shared memory by TMA bulk tensor
  * copies.  -1: not tuned or no such level.  The choice does not change any result.  Setting
  * the environment variable BMG_FORCE_APPLY_TILE to one of these indices before
- * bmg_setup_hierarchy fixes the operator's choice on every level.
+ * bmg_setup_hierarchy fixes the operator's choice on every level; BMG_FORCE_SMOOTHER_TILE
+ * (0-4) fixes the Vanka tile (Vanka hierarchies) or the displacement-Vanka tile (BSR) the
+ * same way.  Out-of-range values select the built-in rule.  Both exist to test every
+ * candidate.
  */
 int bmg_hierarchy_tile(const bmg_hierarchy *h, int level, int kernel);
 

@@ -38,7 +38,10 @@ class MgOpts(C.Structure):
 
 class KrylovOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("x0_is_zero", C.c_int)]
+                ("x0_is_zero", C.c_int), ("arnoldi", C.c_int)]
+
+
+ARNOLDI = {"fp64": 0, "mixed": 1}
 
 
 class SolveInfo(C.Structure):
@@ -242,8 +245,10 @@ class Hierarchy:
         """Tile index chosen at setup for a kernel family on a level (``bmg_hierarchy_tile``)."""
         return lib.bmg_hierarchy_tile(self._h, level, PROF[kernel])
 
-    def fgmres_solve(self, b, x, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True, stream=None):
-        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+    def fgmres_solve(self, b, x, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True, stream=None,
+                     arnoldi="fp64"):
+        """``bmg_fgmres_solve``; ``arnoldi`` is "fp64" (default) or "mixed"."""
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0, ARNOLDI[arnoldi])
         info = SolveInfo()
         _check(lib.bmg_fgmres_solve(self._h, _ptr(b), _ptr(x), C.byref(ko), C.byref(info),
                                     _stream(stream)), "bmg_fgmres_solve")
@@ -253,18 +258,18 @@ class Hierarchy:
                              stream=None):
         """The allocation-free variant: the Krylov workspace is the library's fixed device
         array (``noalloc_capacity()`` doubles); see ``bmg_fgmres_solve_noalloc``."""
-        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0, 0)
         info = SolveInfo()
         _check(lib.bmg_fgmres_solve_noalloc(self._h, _ptr(b), _ptr(x), C.byref(ko), C.byref(info),
                                             _stream(stream)), "bmg_fgmres_solve_noalloc")
         return _info(info)
 
     def fgmres_solve_host(self, b: np.ndarray, x: np.ndarray, rtol=1e-8, restart=50, maxit=500,
-                          x0_is_zero=True, stream=None):
+                          x0_is_zero=True, stream=None, arnoldi="fp64"):
         """Host-buffer variant: ``b`` and ``x`` are float64 numpy arrays (pinned or not)."""
         assert b.dtype == np.float64 and x.dtype == np.float64
         assert b.flags.c_contiguous and x.flags.c_contiguous
-        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0, ARNOLDI[arnoldi])
         info = SolveInfo()
         _check(lib.bmg_fgmres_solve_host(self._h, b.ctypes.data, x.ctypes.data, C.byref(ko),
                                          C.byref(info), _stream(stream)), "bmg_fgmres_solve_host")
@@ -308,11 +313,11 @@ class Batch:
     one graph launch per solve, the FGMRES state of every instance on the device."""
 
     def __init__(self, hierarchies, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True,
-                 autotune=True, stream=None):
+                 autotune=True, stream=None, arnoldi="fp64"):
         self.hierarchies = list(hierarchies)      # keeps them alive
         self.count = len(self.hierarchies)
         arr = (_vp * self.count)(*[h._h for h in self.hierarchies])
-        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0)
+        ko = KrylovOpts(rtol, restart, maxit, 1 if x0_is_zero else 0, ARNOLDI[arnoldi])
         self._b = _vp()
         _check(lib.bmg_batch_create(arr, self.count, C.byref(ko), 1 if autotune else 0,
                                     _stream(stream), C.byref(self._b)), "bmg_batch_create")

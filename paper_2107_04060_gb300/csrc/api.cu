@@ -397,9 +397,15 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
                    [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); }, e0, e1, st);
     if (rc) return rc;
   }
-  if (h->opts.smoother == BMG_VANKA)
+  // BMG_FORCE_SMOOTHER_TILE fixes the Vanka (or, for BSR, the displacement-Vanka) tile
+  const char *force_s = std::getenv("BMG_FORCE_SMOOTHER_TILE");
+  const bool forced = force_s && *force_s;
+  if (h->opts.smoother == BMG_VANKA) {
+    if (forced) { L.tile_vanka = std::atoi(force_s); return BMG_OK; }
     return pick_tile(&L.tile_vanka, 0, 4,
                      [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
+  }
+  if (forced) { L.tile_vanka_u = std::atoi(force_s); return BMG_OK; }
   return pick_tile(&L.tile_vanka_u, 0, 4,
                    [&] { return launch_bsr_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
 }
@@ -635,8 +641,11 @@ extern "C" int bmg_vcycle(bmg_hierarchy *h, const double *r, double *z, void *st
 // ---- FGMRES ----------------------------------------------------------------------------
 static const int kDotBlocks = 152 * 4;
 
-static int ensure_krylov(bmg_hierarchy *h, int m) {
-  if (h->m_alloc >= m) return BMG_OK;
+static int ensure_krylov(bmg_hierarchy *h, int m, bool need32) {
+  if (h->m_alloc >= m) {
+    if (need32 && !h->V32) BMG_CUDA(cudaMalloc(&h->V32, sizeof(float) * vec_len_of(h->sys->n) * (h->m_alloc + 1)));
+    return BMG_OK;
+  }
   cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r); cudaFree(h->V32);
   cudaFree(h->partial); cudaFree(h->dres); cudaFreeHost(h->hres);
   h->V = h->Z = h->w = h->r = h->partial = h->dres = h->hres = nullptr;
@@ -644,7 +653,7 @@ static int ensure_krylov(bmg_hierarchy *h, int m) {
   h->m_alloc = 0;
   const size_t vl = vec_len_of(h->sys->n);
   BMG_CUDA(cudaMalloc(&h->V, sizeof(double) * vl * (m + 1)));
-  BMG_CUDA(cudaMalloc(&h->V32, sizeof(float) * vl * (m + 1)));
+  if (need32) BMG_CUDA(cudaMalloc(&h->V32, sizeof(float) * vl * (m + 1)));
   BMG_CUDA(cudaMalloc(&h->Z, sizeof(double) * vl * m));
   BMG_CUDA(cudaMalloc(&h->w, sizeof(double) * vl));
   BMG_CUDA(cudaMalloc(&h->r, sizeof(double) * vl));
@@ -662,9 +671,12 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
   if (b == x) return arg_error("bmg_fgmres_solve: x may not alias b");
   if (!(o->rtol > 0.0 && o->rtol < 1.0) || o->restart < 1 || o->restart > 200 || o->maxit < 0)
     return arg_error("bmg_fgmres_solve: need 0 < rtol < 1, 1 <= restart <= 200, maxit >= 0");
+  if (o->arnoldi != BMG_ARNOLDI_FP64 && o->arnoldi != BMG_ARNOLDI_MIXED)
+    return arg_error("bmg_fgmres_solve: arnoldi must be BMG_ARNOLDI_FP64 or BMG_ARNOLDI_MIXED");
+  const bool mixed = o->arnoldi == BMG_ARNOLDI_MIXED;
   cudaStream_t st = (cudaStream_t)stream;
   const int m = o->restart;
-  int rc = ensure_krylov(h, m);
+  int rc = ensure_krylov(h, m, mixed);
   if (rc) return rc;
   const bmg_system *s = h->sys;
   const size_t vl = vec_len_of(s->n);
@@ -710,7 +722,8 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &beta, sizeof(double), cudaMemcpyHostToDevice, st));
-    if ((rc = launch_scale2(h->r, h->V, h->V32, h->dres + 3 * (m + 2), vl, st))) return rc;
+    if ((rc = mixed ? launch_scale2(h->r, h->V, h->V32, h->dres + 3 * (m + 2), vl, st)
+                    : launch_scale(h->r, h->V, h->dres + 3 * (m + 2), vl, st))) return rc;
     int k = 0;
     bool stop = false;
     for (int j = 0; j < m && !stop; ++j) {
@@ -719,12 +732,22 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if ((rc = vcycle_any(h, vj, zj, st))) return rc;
       if ((rc = launch_apply<double>(h->fine_op, zj, nullptr, h->w, false, 1, 0, st))) return rc;
       double *d1 = h->dres, *d2 = h->dres + (m + 2), *d3 = h->dres + 2 * (m + 2);
-      // CGS2: h1 = V^T w (from the FP32 copy of V); w -= V h1 (FP64) fused with h2 = V^T w;
-      // w -= V h2 fused with ||w||^2 (both double-float products on the FP32 pipe)
-      if ((rc = launch_dots32(h->V32, ldv, j + 1, h->w, vl, h->partial, kGsMaxBlocks, d1, st))) return rc;
-      if ((rc = launch_update_dots_df(h->w, h->V, ldv, j + 1, d1, vl, h->partial, kGsMaxBlocks, d2, st)))
-        return rc;
-      if ((rc = launch_correct_df_norm(h->w, h->V, ldv, j + 1, d2, vl, h->partial, kDotBlocks, d3, st))) return rc;
+      if (mixed) {
+        // CGS2: h1 = V^T w (from the FP32 copy of V); w -= V h1 (FP64) fused with h2 = V^T w;
+        // w -= V h2 fused with ||w||^2 (both double-float products on the FP32 pipe)
+        if ((rc = launch_dots32(h->V32, ldv, j + 1, h->w, vl, h->partial, kGsMaxBlocks, d1, st))) return rc;
+        if ((rc = launch_update_dots_df(h->w, h->V, ldv, j + 1, d1, vl, h->partial, kGsMaxBlocks, d2, st)))
+          return rc;
+        if ((rc = launch_correct_df_norm(h->w, h->V, ldv, j + 1, d2, vl, h->partial, kDotBlocks, d3, st)))
+          return rc;
+      } else {
+        // CGS2 in FP64: h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with ||w||^2
+        if ((rc = launch_dots_f64(h->w, h->V, ldv, j + 1, vl, h->partial, kGsMaxBlocks, d1, st))) return rc;
+        if ((rc = launch_update_dots_f64(h->w, h->V, ldv, j + 1, d1, vl, h->partial, kGsMaxBlocks, d2, st)))
+          return rc;
+        if ((rc = launch_correct_f64_norm(h->w, h->V, ldv, j + 1, d2, vl, h->partial, kDotBlocks, d3, st)))
+          return rc;
+      }
       BMG_CUDA(cudaMemcpyAsync(hr, h->dres, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
       BMG_CUDA(cudaStreamSynchronize(st));
       const double hn = std::sqrt(hr[2 * (m + 2)]);
@@ -738,8 +761,10 @@ extern "C" int bmg_fgmres_solve(bmg_hierarchy *h, const double *b, double *x,
       if (!finite) { inf.status = BMG_DIVERGED; stop = true; k = j; break; }
       if (hn > 0.0) {
         BMG_CUDA(cudaMemcpyAsync(h->dres + 3 * (m + 2), &Hij(j + 1, j), sizeof(double), cudaMemcpyHostToDevice, st));
-        if ((rc = launch_scale2(h->w, h->V + (size_t)(j + 1) * ldv, h->V32 + (size_t)(j + 1) * ldv,
-                                h->dres + 3 * (m + 2), vl, st))) return rc;
+        if ((rc = mixed ? launch_scale2(h->w, h->V + (size_t)(j + 1) * ldv, h->V32 + (size_t)(j + 1) * ldv,
+                                        h->dres + 3 * (m + 2), vl, st)
+                        : launch_scale(h->w, h->V + (size_t)(j + 1) * ldv, h->dres + 3 * (m + 2), vl, st)))
+          return rc;
       }
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);

@@ -91,15 +91,18 @@ __global__ void __launch_bounds__(kVecThreads) batch_copyout_kernel(const BInst 
 
 // Block-partial products of one Arnoldi pass (or a norm), with the preceding update:
 //   OP_NORM_B: b.b                       OP_NORM_R: r.r (gate_end)
-//   OP_CGS1:   V_q.w (q <= j) from the FP32 copy of V (FP32 products and per-thread sums,
-//              FP64 beyond); also Z_j = z (gate_iter)
-//   OP_CGS2:   w -= V d1 (FP64); V_q.w (q <= j) in double-float arithmetic, w.w
-//   OP_CGS3:   w -= V d2 with the product V d2 in double-float arithmetic; w.w
+//   OP_CGS1:   V_q.w (q <= j); also Z_j = z (gate_iter)
+//   OP_CGS2:   w -= V d1 (FP64); V_q.w (q <= j), w.w
+//   OP_CGS3:   w -= V d2; w.w
+// With df = 0 (BMG_ARNOLDI_FP64) every product is FP64.  With df = 1 (BMG_ARNOLDI_MIXED) the
+// OP_CGS1 products come from the FP32 copy of V (FP32 products and per-thread sums, FP64
+// beyond), and the OP_CGS2 products and the OP_CGS3 product V d2 are formed in double-float
+// arithmetic from the FP64 basis.
 // Products are stored at partial[slot][chunk] (slot q for V_q.w, slot j + 1 for w.w; slot 0
 // for a norm), then summed over the chunks in a fixed order by batch_reduce_kernel.
 __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__restrict__ I,
                                                                 const int *__restrict__ item_inst,
-                                                                int op, int m) {
+                                                                int op, int m, int df) {
   constexpr int G = 8;
   __shared__ double red[G][kVecThreads / 32];
   const int q = item_inst[blockIdx.x];
@@ -117,6 +120,36 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
   double *w = op == OP_NORM_B ? a.B : op == OP_NORM_R ? a.R : a.W;
   double *zj = a.Z + (size_t)s.j * vl;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (op == OP_CGS1 && !df) {
+    for (int q0 = 0; q0 < k; q0 += G) {
+      const int cnt = min(G, k - q0);
+      double acc[G];
+#pragma unroll
+      for (int gi = 0; gi < G; ++gi) acc[gi] = 0.0;
+      for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
+        const double wi = w[i];
+        if (q0 == 0) zj[i] = a.Zc[i];
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi)
+          if (gi < cnt) acc[gi] = fma(a.V[(size_t)(q0 + gi) * vl + i], wi, acc[gi]);
+      }
+#pragma unroll
+      for (int gi = 0; gi < G; ++gi) {
+        double t = acc[gi];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
+        if (lane == 0) red[gi][wid] = t;
+      }
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        double t = 0.0;
+        for (int u = 0; u < kVecThreads / 32; ++u) t += red[threadIdx.x][u];
+        a.partial[(size_t)(q0 + threadIdx.x) * a.nb + chunk] = t;
+      }
+      __syncthreads();
+    }
+    return;
+  }
   if (op == OP_CGS1) {
     const float *V32 = a.V32;
     for (int q0 = 0; q0 < k; q0 += G) {
@@ -149,7 +182,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
     return;
   }
   __shared__ float2 hf[kMaxBasis];                 // OP_CGS3: the coefficients, head and tail
-  if (op == OP_CGS3) {
+  if (op == OP_CGS3 && df) {
     for (int p = threadIdx.x; p < k; p += kVecThreads) {
       float2 t;
       split_f64(h[p], t.x, t.y);
@@ -160,14 +193,18 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
   const int nd = vdots ? k + 1 : 1;
   for (int q0 = 0; q0 < nd; q0 += G) {
     const int cnt = min(G, nd - q0);
-    float sh[G], sl[G];                            // V_q.w: double-float sums
+    float sh[G], sl[G];                            // V_q.w: double-float sums (df)
+    double acc[G];                                 // V_q.w: FP64 sums (!df)
     double accw = 0.0;                             // w.w in FP64
 #pragma unroll
-    for (int gi = 0; gi < G; ++gi) sh[gi] = sl[gi] = 0.f;
+    for (int gi = 0; gi < G; ++gi) {
+      sh[gi] = sl[gi] = 0.f;
+      acc[gi] = 0.0;
+    }
     for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
       double wi = w[i];
       if (q0 == 0) {
-        if (op == OP_CGS3) {
+        if (op == OP_CGS3 && df) {
           float ch = 0.f, cl = 0.f;
           for (int p = 0; p < k; ++p) {
             float vh, vt;
@@ -182,15 +219,19 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
         }
       }
       float wh = 0.f, wl = 0.f;
-      if (vdots) split_f64(wi, wh, wl);
+      if (vdots && df) split_f64(wi, wh, wl);
 #pragma unroll
       for (int gi = 0; gi < G; ++gi) {
         if (gi < cnt) {
           const int p = vdots ? q0 + gi : k;
           if (p < k) {
-            float vh, vt;
-            split_f64(a.V[(size_t)p * vl + i], vh, vt);
-            df_dot_step(vh, vt, wh, wl, sh[gi], sl[gi]);
+            if (df) {
+              float vh, vt;
+              split_f64(a.V[(size_t)p * vl + i], vh, vt);
+              df_dot_step(vh, vt, wh, wl, sh[gi], sl[gi]);
+            } else {
+              acc[gi] = fma(a.V[(size_t)p * vl + i], wi, acc[gi]);
+            }
           } else {
             accw = fma(wi, wi, accw);
           }
@@ -200,7 +241,7 @@ __global__ void __launch_bounds__(kVecThreads) batch_vec_kernel(const BInst *__r
 #pragma unroll
     for (int gi = 0; gi < G; ++gi) {
       const int p = vdots ? q0 + gi : k;
-      double t = p < k ? f32_to_f64_bits(sh[gi]) + f32_to_f64_bits(sl[gi]) : accw;
+      double t = p < k ? (df ? f32_to_f64_bits(sh[gi]) + f32_to_f64_bits(sl[gi]) : acc[gi]) : accw;
 #pragma unroll
       for (int sh = 16; sh > 0; sh >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sh);
       if (lane == 0) red[gi][wid] = t;
@@ -265,13 +306,13 @@ __global__ void __launch_bounds__(kVecThreads) batch_basis_kernel(const BInst *_
   const double den = s.fresh ? s.beta : s.hnext;
   const double dinv = den != 0.0 ? 1.0 / den : 0.0;
   double *vj = a.V + (size_t)s.j * a.vl;
-  float *vj32 = a.V32 + (size_t)s.j * a.vl;
+  float *vj32 = a.V32 ? a.V32 + (size_t)s.j * a.vl : nullptr;
   const size_t c0 = (size_t)(blockIdx.x - a.item0) * kChunk;
   const size_t c1 = min(a.vl, c0 + kChunk);
   for (size_t i = c0 + threadIdx.x; i < c1; i += kVecThreads) {
     const double v = src[i] * dinv;
     vj[i] = v;
-    vj32[i] = f64_to_f32_trunc(v);
+    if (vj32) vj32[i] = f64_to_f32_trunc(v);
     a.Q[i] = v;
   }
 }
@@ -434,6 +475,7 @@ using namespace bmg;
 // ---- batch object -----------------------------------------------------------------------
 struct bmg_batch {
   int count = 0, m = 0, maxit = 0, x0_zero = 1;
+  int df = 0;                           // 1: mixed Arnoldi (BMG_ARNOLDI_MIXED)
   double rtol = 0.0;
   std::vector<bmg_hierarchy *> hs;
   std::vector<size_t> vl;
@@ -497,7 +539,7 @@ static int record_trip(bmg_batch *bt, cudaStream_t st, cudaGraphConditionalHandl
   BMG_CHECK_LAUNCH("batch_axpy_kernel");
   for (const auto &L : bt->resid)
     if ((rc = run_launch(bt, L, st))) return rc;
-  batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, OP_NORM_R, m);
+  batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, OP_NORM_R, m, bt->df);
   BMG_CHECK_LAUNCH("batch_vec_kernel");
   batch_reduce_kernel<<<dim3(1, C), 128, 0, st>>>(bt->d_inst, OP_NORM_R, m);
   BMG_CHECK_LAUNCH("batch_reduce_kernel");
@@ -511,7 +553,7 @@ static int record_trip(bmg_batch *bt, cudaStream_t st, cudaGraphConditionalHandl
   for (const auto &L : bt->wapply)
     if ((rc = run_launch(bt, L, st))) return rc;
   for (int op = OP_CGS1; op <= OP_CGS3; ++op) {
-    batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, op, m);
+    batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, op, m, bt->df);
     BMG_CHECK_LAUNCH("batch_vec_kernel");
     batch_reduce_kernel<<<dim3(op == OP_CGS3 ? 1 : m + 1, C), 128, 0, st>>>(bt->d_inst, op, m);
     BMG_CHECK_LAUNCH("batch_reduce_kernel");
@@ -528,7 +570,7 @@ static int record_prologue(bmg_batch *bt, cudaStream_t st) {
   batch_copyin_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst,
                                                      (const double *const *)bt->d_user, bt->x0_zero, C);
   BMG_CHECK_LAUNCH("batch_copyin_kernel");
-  batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, OP_NORM_B, bt->m);
+  batch_vec_kernel<<<items, kVecThreads, 0, st>>>(bt->d_inst, bt->d_item_inst, OP_NORM_B, bt->m, bt->df);
   BMG_CHECK_LAUNCH("batch_vec_kernel");
   batch_reduce_kernel<<<dim3(1, C), 128, 0, st>>>(bt->d_inst, OP_NORM_B, bt->m);
   BMG_CHECK_LAUNCH("batch_reduce_kernel");
@@ -684,6 +726,8 @@ extern "C" int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_k
   if (count < 1 || count > 4096) return batch_error("bmg_batch_create: need 1 <= count <= 4096");
   if (!(o->rtol > 0.0 && o->rtol < 1.0) || o->restart < 1 || o->restart > 200 || o->maxit < 0)
     return batch_error("bmg_batch_create: need 0 < rtol < 1, 1 <= restart <= 200, maxit >= 0");
+  if (o->arnoldi != BMG_ARNOLDI_FP64 && o->arnoldi != BMG_ARNOLDI_MIXED)
+    return batch_error("bmg_batch_create: arnoldi must be BMG_ARNOLDI_FP64 or BMG_ARNOLDI_MIXED");
   std::set<const bmg_hierarchy *> uniq;
   for (int q = 0; q < count; ++q) {
     const bmg_hierarchy *h = hs[q];
@@ -712,6 +756,7 @@ extern "C" int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_k
   bt->maxit = o->maxit;
   bt->rtol = o->rtol;
   bt->x0_zero = o->x0_is_zero ? 1 : 0;
+  bt->df = o->arnoldi == BMG_ARNOLDI_MIXED ? 1 : 0;
   bt->hs.assign(hs, hs + count);
   const int m = bt->m;
   // per-instance vectors and FGMRES arrays
@@ -749,9 +794,12 @@ extern "C" int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_k
         (rc = dalloc(&a.cs, m + 1)) || (rc = dalloc(&a.sn, m + 1)) || (rc = dalloc(&a.g, m + 1)) ||
         (rc = dalloc(&a.y, m + 1)))
       return fail(rc);
-    if (cudaMalloc(&a.V32, sizeof(float) * a.vl * (m + 1)) != cudaSuccess)
-      return fail(cuda_fail(cudaErrorMemoryAllocation, "batch buffers"));
-    bt->fbufs.push_back(a.V32);
+    a.V32 = nullptr;
+    if (bt->df) {
+      if (cudaMalloc(&a.V32, sizeof(float) * a.vl * (m + 1)) != cudaSuccess)
+        return fail(cuda_fail(cudaErrorMemoryAllocation, "batch buffers"));
+      bt->fbufs.push_back(a.V32);
+    }
     a.Q = (double *)L0.rhs;
     a.Zc = (double *)L0.z;
     a.s = bt->d_state + q;

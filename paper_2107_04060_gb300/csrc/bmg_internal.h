@@ -334,12 +334,18 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
 // their grids (the partial-sum buffer holds kGsMaxBlocks * k entries).
 constexpr int kMaxBasisVecs = 200;
 constexpr int kDotsKQ = 16, kDotsMaxTY = 13;      // dots32
-constexpr int kUpdKQ = 12, kUpdMaxTY = 17;        // update_dots_df
+constexpr int kUpdKQ = 12, kUpdMaxTY = 17;        // gs_pass (update_dots_df/_f64, dots_f64)
 constexpr int kGsMaxBlocks = 152 * 32;
 static_assert(kDotsKQ * kDotsMaxTY >= kMaxBasisVecs && kUpdKQ * kUpdMaxTY >= kMaxBasisVecs,
               "Gram-Schmidt kernels must cover every restart length");
 int launch_update_dots_df(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
                          double *partial, int max_blocks, double *out, cudaStream_t st);
+int launch_update_dots_f64(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                           double *partial, int max_blocks, double *out, cudaStream_t st);
+int launch_dots_f64(const double *w, const double *V, size_t ldv, int k, size_t n, double *partial,
+                    int max_blocks, double *out, cudaStream_t st);
+int launch_correct_f64_norm(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                            double *partial, int nblocks, double *out, cudaStream_t st);
 int launch_scale(const double *w, double *v, const double *s, size_t n, cudaStream_t st);
 int launch_scale2(const double *w, double *v, float *v32, const double *s, size_t n, cudaStream_t st);
 int launch_dots32(const float *V, size_t ldv, int k, const double *w, size_t n, double *partial,

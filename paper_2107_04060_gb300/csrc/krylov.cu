@@ -2,6 +2,7 @@
 // set of basis vectors with a deterministic second-stage reduction, the Gram-Schmidt
 // update, scaling, the solution update x += Z y, and precision conversion.
 #include <atomic>
+#include <string>
 
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
@@ -147,7 +148,7 @@ static int resident_blocks(Kern kern, int ty, size_t smem, std::atomic<int> *cac
 // component along the basis: the second pass measures and removes what it left, and the
 // Hessenberg column is the sum of the two passes' coefficients.
 //
-// Layout as update_dots_df_kernel's: blockDim = (32, TY), lane x of warp y owns elements
+// Layout as gs_pass_kernel's: blockDim = (32, TY), lane x of warp y owns elements
 // base + 2x, base + 2x + 1 (8-byte loads of V32, 16-byte loads of w) and the vectors
 // q = y * KQ .. y * KQ + KQ - 1.  w is converted to FP32 once per element (integer
 // truncation, no FP64 pipe work), and the next batch's loads are issued before the current
@@ -239,44 +240,54 @@ int launch_update(double *w, const double *V, size_t ldv, int k, const double *h
   return BMG_OK;
 }
 
-// w <- w - sum_q h[q] V_q (FP64 basis, FP64 products: the Hessenberg coefficients must describe
-// exactly what is subtracted), fused with the block-partial products V_q . w_new (q < k) of
-// the second Gram-Schmidt pass.  Those products are formed on the FP32 pipe in double-float
-// arithmetic (each FP64 value split exactly into a truncated FP32 head and an FP32 tail,
-// head products made exact with a fused multiply-add, running sums kept as an unevaluated
+// One pass of classical Gram-Schmidt over the basis V_0 .. V_{k-1}, optionally preceded by the
+// update of the previous pass:
+//   UPD:  w <- w - sum_q h[q] V_q (FP64 basis, FP64 products: the Hessenberg coefficients must
+//         describe exactly what is subtracted), written back to w;
+//   then  block-partial products V_q . w (q < k) of the (updated) w.
+// The products are formed either in FP64 (DF = false: plain FP64 Arnoldi, one FP64 fused
+// multiply-add per element and vector) or on the FP32 pipe in double-float arithmetic (DF =
+// true: each FP64 value split into a truncated FP32 head and an FP32 tail carrying the next 23
+// bits, head products made exact with a fused multiply-add, running sums kept as an unevaluated
 // FP32 pair by the error-free two-sum), accurate to about 2^-46 relative to the sum of the
-// products' magnitudes: the second pass keeps the new basis vector orthogonal to the old ones
-// far below FP32 rounding, while the FP64 pipe does only the update's k fused multiply-adds
-// per element (the FP64 form of the pass does 2k).  V is streamed from HBM once.
+// products' magnitudes; then the FP64 pipe does only the update's k fused multiply-adds per
+// element.  V is streamed from HBM once per pass.
 //
 // Layout: blockDim = (32, TY).  Lane x of warp y owns element base + x and the basis vectors
 // q = y * KQ .. y * KQ + KQ - 1: a warp's loads of one vector are one coalesced 256-byte
-// row, each thread holds at most KQ values, and the TY partial updates of an element meet
-// in shared memory.  A warp owns its vectors' products, so no cross-warp reduction is needed.
-// The next batch's loads are issued before the current batch's arithmetic.
-template <int KQ>
-__global__ void __launch_bounds__(32 * kUpdMaxTY) update_dots_df_kernel(double *__restrict__ w, const double *__restrict__ V,
-                                                                     size_t ldv, int k, const double *__restrict__ h,
-                                                                     size_t n, double *__restrict__ partial) {
+// row, each thread holds at most KQ values, and (UPD) the TY partial updates of an element
+// meet in shared memory.  A warp owns its vectors' products, so no cross-warp reduction is
+// needed.  The next batch's loads are issued before the current batch's arithmetic.
+template <int KQ, bool DF, bool UPD>
+__global__ void __launch_bounds__(32 * kUpdMaxTY) gs_pass_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                                 size_t ldv, int k, const double *__restrict__ h,
+                                                                 size_t n, double *__restrict__ partial) {
   pdl_enter();
   extern __shared__ double upd_smem[];
   const int TY = blockDim.y, x = threadIdx.x, y = threadIdx.y;
-  double *hs = upd_smem;                       // [k]
-  double *part = hs + k;                       // [TY][32]
-  float2 *wsh = reinterpret_cast<float2 *>(part + 32 * TY);   // [32] head and tail of w_new
-  for (int q = y * 32 + x; q < k; q += 32 * TY) hs[q] = h[q];
-  __syncthreads();
+  double *hs = upd_smem;                       // [k]      (UPD)
+  double *part = hs + k;                       // [TY][32] (UPD)
+  double *wsd = part + 32 * TY;                // [32] updated w (UPD, FP64 products)
+  float2 *wsh = reinterpret_cast<float2 *>(wsd);   // [32] its head and tail (UPD, DF)
+  if (UPD) {
+    for (int q = y * 32 + x; q < k; q += 32 * TY) hs[q] = h[q];
+    __syncthreads();
+  }
   const int q0 = y * KQ;
   const size_t stride = (size_t)gridDim.x * 32;
-  float sh[KQ], sl[KQ];                          // double-float running sums of V_q . w_new
+  float sh[KQ], sl[KQ];                          // DF: double-float running sums of V_q . w
+  double acc[KQ];                                // FP64 running sums
 #pragma unroll
-  for (int j = 0; j < KQ; ++j) sh[j] = sl[j] = 0.f;
+  for (int j = 0; j < KQ; ++j) {
+    sh[j] = sl[j] = 0.f;
+    acc[j] = 0.0;
+  }
   double vn[KQ];
   double wn = 0.0;
   auto load = [&](size_t base) {
     const size_t i = base + x;
     const bool valid = i < n;
-    wn = (y == 0 && valid) ? w[i] : 0.0;
+    wn = ((!UPD || y == 0) && valid) ? w[i] : 0.0;
 #pragma unroll
     for (int j = 0; j < KQ; ++j)
       vn[j] = (q0 + j < k && valid) ? V[(size_t)(q0 + j) * ldv + i] : 0.0;
@@ -291,33 +302,48 @@ __global__ void __launch_bounds__(32 * kUpdMaxTY) update_dots_df_kernel(double *
     if (base + stride < n) load(base + stride);
     const size_t i = base + x;
     const bool valid = i < n;
+    double wv = p;                               // the w the products are taken with
+    float2 ws = make_float2(0.f, 0.f);
+    if (UPD) {
 #pragma unroll
-    for (int j = 0; j < KQ; ++j)
-      if (q0 + j < k) p = fma(-hs[q0 + j], vc[j], p);      // warp-uniform
-    float2 ws;
-    if (TY == 1) {
-      if (valid) w[i] = p;
-      split_f64(p, ws.x, ws.y);
-    } else {
-      part[y * 32 + x] = p;
-      __syncthreads();
-      if (y == 0) {
-        double s = part[x];
-        for (int u = 1; u < TY; ++u) s += part[u * 32 + x];
-        if (valid) w[i] = s;
-        float2 t;
-        split_f64(s, t.x, t.y);
-        wsh[x] = t;
+      for (int j = 0; j < KQ; ++j)
+        if (q0 + j < k) p = fma(-hs[q0 + j], vc[j], p);      // warp-uniform
+      if (TY == 1) {
+        if (valid) w[i] = p;
+        wv = p;
+        if (DF) split_f64(p, ws.x, ws.y);
+      } else {
+        part[y * 32 + x] = p;
+        __syncthreads();
+        if (y == 0) {
+          double s = part[x];
+          for (int u = 1; u < TY; ++u) s += part[u * 32 + x];
+          if (valid) w[i] = s;
+          if (DF) {
+            float2 t;
+            split_f64(s, t.x, t.y);
+            wsh[x] = t;
+          } else {
+            wsd[x] = s;
+          }
+        }
+        __syncthreads();
+        if (DF) ws = wsh[x];
+        else wv = wsd[x];
       }
-      __syncthreads();
-      ws = wsh[x];
+    } else if (DF) {
+      split_f64(p, ws.x, ws.y);
     }
 #pragma unroll
     for (int j = 0; j < KQ; ++j) {
       if (q0 + j < k) {
-        float vh, vl;
-        split_f64(vc[j], vh, vl);
-        df_dot_step(vh, vl, ws.x, ws.y, sh[j], sl[j]);
+        if (DF) {
+          float vh, vl;
+          split_f64(vc[j], vh, vl);
+          df_dot_step(vh, vl, ws.x, ws.y, sh[j], sl[j]);
+        } else {
+          acc[j] = fma(vc[j], wv, acc[j]);
+        }
       }
     }
   }
@@ -325,7 +351,7 @@ __global__ void __launch_bounds__(32 * kUpdMaxTY) update_dots_df_kernel(double *
   for (int j = 0; j < KQ; ++j) {
     const int q = q0 + j;
     if (q < k) {                                 // warp-uniform
-      double a = f32_to_f64_bits(sh[j]) + f32_to_f64_bits(sl[j]);
+      double a = DF ? f32_to_f64_bits(sh[j]) + f32_to_f64_bits(sl[j]) : acc[j];
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
       if (x == 0) partial[(size_t)q * gridDim.x + blockIdx.x] = a;
@@ -333,33 +359,52 @@ __global__ void __launch_bounds__(32 * kUpdMaxTY) update_dots_df_kernel(double *
   }
 }
 
-static size_t update_dots_df_smem(int k, int ty) {
-  return sizeof(double) * ((size_t)k + 32 * (size_t)ty) + sizeof(float2) * 32;
+static size_t gs_pass_smem(int k, int ty, bool upd) {
+  return upd ? sizeof(double) * ((size_t)k + 32 * (size_t)ty + 32) : 0;
 }
 
-// out[0..k-1] = V_q . w_new (double-float products) after w_new = w - V h (FP64);
-// 1 <= k <= kUpdKQ * kUpdMaxTY.  partial holds max_blocks * k entries.
-int launch_update_dots_df(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
-                          double *partial, int max_blocks, double *out, cudaStream_t st) {
+template <bool DF, bool UPD>
+static int launch_gs_pass(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                          double *partial, int max_blocks, double *out, cudaStream_t st, const char *what) {
   if (k <= 0 || k > kUpdKQ * kUpdMaxTY) return BMG_ERR_ARG;
   static std::atomic<int> cache[kUpdMaxTY + 1];
   const int ty = (k + kUpdKQ - 1) / kUpdKQ;
-  int nb = resident_blocks(update_dots_df_kernel<kUpdKQ>, ty, update_dots_df_smem(kUpdKQ * ty, ty), cache);
+  auto kern = gs_pass_kernel<kUpdKQ, DF, UPD>;
+  int nb = resident_blocks(kern, ty, gs_pass_smem(kUpdKQ * ty, ty, UPD), cache);
   if (nb <= 0) {
-    set_error("update_dots_df: occupancy query failed");
+    set_error(std::string(what) + ": occupancy query failed");
     return BMG_ERR_CUDA;
   }
   const size_t nbatch = (n + 31) / 32;
   if ((size_t)nb > nbatch) nb = (int)nbatch;
   if (nb > max_blocks) nb = max_blocks;
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
-  BMG_CUDA(launch_pdl(update_dots_df_kernel<kUpdKQ>, dim3(nb), dim3(32, ty), update_dots_df_smem(k, ty), st,
-                      w, V, ldv, k, h, n, partial));
-  BMG_CHECK_LAUNCH("update_dots_df_kernel");
+  BMG_CUDA(launch_pdl(kern, dim3(nb), dim3(32, ty), gs_pass_smem(k, ty, UPD), st, w, V, ldv, k, h, n, partial));
+  BMG_CHECK_LAUNCH(what);
   BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(k), dim3(256), 0, st, (const double *)partial, nb, k, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");
   return BMG_OK;
+}
+
+// out[0..k-1] = V_q . w_new (double-float products) after w_new = w - V h (FP64);
+// 1 <= k <= kUpdKQ * kUpdMaxTY.  partial holds max_blocks * k entries.
+int launch_update_dots_df(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                          double *partial, int max_blocks, double *out, cudaStream_t st) {
+  return launch_gs_pass<true, true>(w, V, ldv, k, h, n, partial, max_blocks, out, st, "update_dots_df");
+}
+
+// out[0..k-1] = V_q . w_new (FP64 products) after w_new = w - V h (FP64)
+int launch_update_dots_f64(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                           double *partial, int max_blocks, double *out, cudaStream_t st) {
+  return launch_gs_pass<false, true>(w, V, ldv, k, h, n, partial, max_blocks, out, st, "update_dots_f64");
+}
+
+// out[0..k-1] = V_q . w (FP64 products; w is only read): the first pass of the FP64 Arnoldi
+int launch_dots_f64(const double *w, const double *V, size_t ldv, int k, size_t n, double *partial,
+                    int max_blocks, double *out, cudaStream_t st) {
+  return launch_gs_pass<false, false>(const_cast<double *>(w), V, ldv, k, nullptr, n, partial, max_blocks,
+                                      out, st, "dots_f64");
 }
 
 // v = w / s[0]   (s on the device; s[0] == 0 leaves v = 0)
@@ -430,6 +475,55 @@ int launch_correct_df_norm(double *w, const double *V, size_t ldv, int k, const 
   BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
   BMG_CUDA(launch_pdl(correct_df_norm_kernel, dim3(nblocks), dim3(256), 0, st, w, V, ldv, k, h, n, partial));
   BMG_CHECK_LAUNCH("correct_df_norm_kernel");
+  BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(1), dim3(256), 0, st, (const double *)partial, nblocks, 1, out));
+  BMG_PROF_END(st, 0.0);
+  BMG_CHECK_LAUNCH("reduce_partials_kernel");
+  return BMG_OK;
+}
+
+// Last Gram-Schmidt correction of the FP64 Arnoldi: w <- w - V h (FP64 products), fused with
+// the block-partial sums of w.w.  Two elements per thread (16-byte loads of V and w).
+__global__ void __launch_bounds__(256) correct_f64_norm_kernel(double *__restrict__ w, const double *__restrict__ V,
+                                                               size_t ldv, int k, const double *__restrict__ h,
+                                                               size_t n, double *__restrict__ partial) {
+  pdl_enter();
+  __shared__ double hs[kMaxBasisVecs];
+  __shared__ double red[8];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  const size_t n2 = n / 2;                         // n and ldv are even
+  double2 *w2 = reinterpret_cast<double2 *>(w);
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    double2 wi = w2[i];
+#pragma unroll 4
+    for (int q = 0; q < k; ++q) {
+      const double2 v = reinterpret_cast<const double2 *>(V + (size_t)q * ldv)[i];
+      wi.x = fma(-hs[q], v.x, wi.x);
+      wi.y = fma(-hs[q], v.y, wi.y);
+    }
+    w2[i] = wi;
+    acc = fma(wi.x, wi.x, fma(wi.y, wi.y, acc));
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < 8; ++u) t += red[u];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// out[0] = ||w_new||^2 after w_new = w - V h (FP64); 1 <= k <= kMaxBasisVecs, n and ldv even
+int launch_correct_f64_norm(double *w, const double *V, size_t ldv, int k, const double *h, size_t n,
+                            double *partial, int nblocks, double *out, cudaStream_t st) {
+  if (k <= 0 || k > kMaxBasisVecs || (n & 1) || (ldv & 1)) return BMG_ERR_ARG;
+  BMG_PROF_BEGIN(BMG_PROF_KRYLOV, 0, st);
+  BMG_CUDA(launch_pdl(correct_f64_norm_kernel, dim3(nblocks), dim3(256), 0, st, w, V, ldv, k, h, n, partial));
+  BMG_CHECK_LAUNCH("correct_f64_norm_kernel");
   BMG_CUDA(launch_pdl(reduce_partials_kernel, dim3(1), dim3(256), 0, st, (const double *)partial, nblocks, 1, out));
   BMG_PROF_END(st, 0.0);
   BMG_CHECK_LAUNCH("reduce_partials_kernel");

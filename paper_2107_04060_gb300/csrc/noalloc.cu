@@ -2,11 +2,12 @@
 // library is loaded, for callers that cannot allocate device memory while they run (see
 // bmg_fgmres_solve_noalloc in include/biotmg.h).
 //
-// The algorithm and the kernels are those of bmg_fgmres_solve: right-preconditioned
+// The algorithm is that of bmg_fgmres_solve with the FP64 Arnoldi: right-preconditioned
 // FGMRES(m), one V-cycle of the hierarchy per iteration, classical Gram-Schmidt with one
-// re-orthogonalisation pass.  Only the storage differs: the basis V, the preconditioned
-// vectors Z, the work vectors and the reduction buffers are carved out of
-// g_noalloc_scratch instead of buffers the hierarchy allocates on first use.
+// re-orthogonalisation pass in FP64 (here as separate product and update kernels).  The
+// storage differs: the basis V, the preconditioned vectors Z, the work vectors and the
+// reduction buffers are carved out of g_noalloc_scratch instead of buffers the hierarchy
+// allocates on first use.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -192,6 +193,14 @@ extern "C" int bmg_fgmres_solve_noalloc(bmg_hierarchy *h, const double *b, doubl
     BMG_CUDA(cudaStreamSynchronize(st));
   }
   BMG_CUDA(cudaStreamSynchronize(st));
+  if (h->opts.precision == BMG_FP32) {         // a timed-out TMA wait leaves its CTA's output unset
+    int flag = 0;
+    BMG_CUDA(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & kErrTmaTimeout) {
+      set_error("bmg_fgmres_solve_noalloc: a bulk-copy wait in the FP32 operator timed out");
+      return BMG_ERR_CUDA;
+    }
+  }
   inf.relres_est = est;
   inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;

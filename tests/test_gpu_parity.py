@@ -154,7 +154,8 @@ def test_vcycle_parity(bmg, n, smoother, omega, kind):
 
 @pytest.mark.parametrize("lam,K", [(1.0, 1.0), (1e4, 1e-6), (1e6, 1.0)])
 @pytest.mark.parametrize("smoother,omega", [("vanka", 0.7), ("bsr", 0.7)])
-def test_fgmres_parity(bmg, lam, K, smoother, omega):
+@pytest.mark.parametrize("arnoldi", ["fp64", "mixed"])
+def test_fgmres_parity(bmg, lam, K, smoother, omega, arnoldi):
     import torch
     n = 32
     p = dict(lam=lam, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
@@ -166,7 +167,7 @@ def test_fgmres_parity(bmg, lam, K, smoother, omega):
     f = synthetic.rhs(n, 0)
     b = dev(bmg, n, f)
     x = torch.zeros_like(b)
-    info = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=300)
+    info = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=300, arnoldi=arnoldi)
     A = H.levels[0].A
     bo = H.levels[0].mesh.pack(f)
     xo, oinfo = krylov.fgmres(A, bo, H.vcycle, rtol=1e-8, restart=50, maxit=300)
