@@ -166,8 +166,8 @@ def element_matrix(parts: dict, prm: Params, kinv: float) -> np.ndarray:
     return E
 
 
-def reference_triangles(n: int):
-    """The two triangle shapes of the mesh (L and U of cell (0, 0))."""
+def reference_triangles(n: float):
+    """The two triangle shapes of the mesh (L and U of cell (0, 0)); spacing h = 1/n."""
     h = 1.0 / n
     out = {}
     for o in ("L", "U"):
@@ -176,15 +176,18 @@ def reference_triangles(n: int):
     return out
 
 
-def assemble(mesh: Mesh, prm: Params, kinv_L: np.ndarray, kinv_U: np.ndarray) -> sp.csr_matrix:
+def assemble(mesh: Mesh, prm: Params, kinv_L: np.ndarray, kinv_U: np.ndarray,
+             h: float = None) -> sp.csr_matrix:
     """Global operator on all DoFs, constrained rows and columns removed (zeroed).
 
     ``kinv_L``, ``kinv_U``: per-triangle K^{-1} arrays ``(n, n)`` indexed ``[j, i]``.
     Triangles of equal shape share all element integrals; only the RT0 mass is scaled by
     the triangle's K^{-1}.  Element loop vectorised over triangles of one shape.
+    ``h`` (default 1/n) overrides the cell size: the local Fourier analysis reads the
+    interior stencils of a grid with spacing h from a small patch of cells.
     """
     n = mesh.n
-    tris = reference_triangles(n)
+    tris = reference_triangles(n if h is None else 1.0 / h)
     rows, cols, vals = [], [], []
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     for o in ("L", "U"):

@@ -1,0 +1,70 @@
+"""Pins of the two-grid local Fourier analysis (oracle/lfa.py) against the paper (CPU only).
+
+* Table 2 (additive Vanka V(2,2), h = 1/64, E = 3e4, alpha = 1, mu_f = 1, M = 1e6, tau = 1,
+  K = kI, k = 1): rho_LFA = 0.410 at nu = 0.4 with omega = 0.80, 0.600 at nu = 0.499 with
+  omega = 0.72, 0.705 at nu = 0 with omega = 0.92; the brute-force optimum over omega in
+  steps of 0.02 is the printed omega_opt (0.80 at nu = 0.4).
+* Table 3 (inexact Braess-Sarazin V(1,1), k = 1): rho_LFA = 0.772 at nu = 0.49 with
+  (omega_J, omega) = (1.21, 0.69), 0.648 at nu = 0 with (1.10, 0.72).
+* Sec. 4.3: omega = 0.9 with Vanka diverges for nu > 0.2 (rho_LFA > 1 at nu = 0.45).
+* Nested-space identities of the symbols (exact for constant K): the Galerkin product of
+  the RT0 mass, of B_w and of the P0 mass equals the rediscretised coarse symbol, which
+  checks the restriction symbol's phases and the 1/4 of the interpolation symbol.
+
+The paper prints three decimals; the pins allow 1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, lfa
+
+
+def paper(nu):
+    return fem.Params.from_paper(3e4, nu, tau=1.0, alpha=1.0, inv_M=1e-6)
+
+
+@pytest.fixture(scope="module")
+def vanka_04():
+    return lfa.TwoGrid(paper(0.4), 1.0, 1 / 64, "vanka")
+
+
+@pytest.mark.parametrize("nu,omega,want", [(0.4, 0.80, 0.410), (0.499, 0.72, 0.600), (0.0, 0.92, 0.705)])
+def test_table2_vanka_rho_lfa(nu, omega, want):
+    tg = lfa.TwoGrid(paper(nu), 1.0, 1 / 64, "vanka")
+    assert tg.rho(omega, 2, 2) == pytest.approx(want, abs=1e-3)
+
+
+@pytest.mark.parametrize("nu,omega_J,omega,want", [(0.49, 1.21, 0.69, 0.772), (0.0, 1.10, 0.72, 0.648)])
+def test_table3_bsr_rho_lfa(nu, omega_J, omega, want):
+    tg = lfa.TwoGrid(paper(nu), 1.0, 1 / 64, "bsr")
+    assert tg.rho(omega, 1, 1, omega_J) == pytest.approx(want, abs=1e-3)
+
+
+def test_table2_omega_opt(vanka_04):
+    om, rho = lfa.optimise_omega(vanka_04, 2, 2, omegas=np.round(np.arange(0.70, 0.9001, 0.02), 2))
+    assert om == pytest.approx(0.80)
+    assert rho == pytest.approx(0.410, abs=1e-3)
+
+
+def test_vanka_omega09_diverges_for_large_nu():
+    tg = lfa.TwoGrid(paper(0.45), 1.0, 1 / 64, "vanka")
+    assert tg.rho(0.9, 2, 2) > 1.0
+
+
+def test_nested_galerkin_identities_of_the_symbols(vanka_04):
+    tg = vanka_04
+    w = np.asarray(lfa.W_IDX)
+    p = np.asarray(lfa.P_IDX)
+    nt = lfa.NT
+    rows_w = np.concatenate([a * nt + w for a in range(4)])
+    rows_p = np.concatenate([a * nt + p for a in range(4)])
+    R, L, P, AH = tg.Rb, tg.Lb, tg.Pb, tg.AH
+    # R_w (tau M_w) P_w = (tau M_w)_2h
+    g = R[:, w][:, :, rows_w] @ L[:, rows_w][:, :, rows_w] @ P[:, rows_w][:, :, w]
+    assert np.abs(g - AH[:, w][:, :, w]).max() <= 1e-12 * np.abs(AH[:, w][:, :, w]).max()
+    # R_p (tau B_w) P_w = (tau B_w)_2h
+    g = R[:, p][:, :, rows_p] @ L[:, rows_p][:, :, rows_w] @ P[:, rows_w][:, :, w]
+    assert np.abs(g - AH[:, p][:, :, w]).max() <= 1e-12 * np.abs(AH[:, p][:, :, w]).max()
+    # R_p (-(1/M) M_p) P_p = (-(1/M) M_p)_2h
+    g = R[:, p][:, :, rows_p] @ L[:, rows_p][:, :, rows_p] @ P[:, rows_p][:, :, p]
+    assert np.abs(g - AH[:, p][:, :, p]).max() <= 1e-12 * np.abs(AH[:, p][:, :, p]).max()
