@@ -130,6 +130,10 @@ typedef struct {
   double p_shift;   /* >= 0: -p_shift * |T| is added to every P0 diagonal entry of the
                        Vanka patch matrices (the regularisation of Sec. 5.3 for 1/M = 0;
                        0 = exact patch solves)                                          */
+  int gamma;        /* coarse-grid cycles per level: 0 or 1 = V-cycle (Sec. 3), 2 = W-cycle
+                       (the remedy the discussion of Table 4 suggests for multilevel inexact
+                       BSR): the coarse problem is approximated by two cycles, the second on
+                       the residual the first leaves; the coarsest solve is direct either way */
 } bmg_mg_opts;
 
 /*
@@ -145,7 +149,8 @@ int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, void *stream,
                         bmg_hierarchy **out);
 
 /*
- * bmg_vcycle -- z = M^{-1} r: one V(nu1, nu2) cycle from a zero initial guess (Sec. 3).
+ * bmg_vcycle -- z = M^{-1} r: one V(nu1, nu2) cycle (W-cycle if gamma = 2) from a zero
+ * initial guess (Sec. 3).
  * r, z: device vectors (bmg_vector_len(n) doubles, FP64 whatever the V-cycle precision;
  * an FP32 hierarchy converts on entry and exit).  z may not alias r.
  */
@@ -266,7 +271,8 @@ size_t bmg_noalloc_capacity(void);
  *
  * bmg_batch_create(hs, count, o, autotune, stream, out)
  *   hs[count]: distinct hierarchies from bmg_setup_hierarchy, all with smoother BMG_VANKA,
- *     precision BMG_FP64, nu1 >= 1 and the same nu1, nu2 and n_coarse (omega may differ).
+ *     precision BMG_FP64, V-cycles (gamma 0 or 1), nu1 >= 1 and the same nu1, nu2 and
+ *     n_coarse (omega may differ).
  *     The batch borrows their level data and work vectors: keep them alive, and do not use
  *     them in other solves while a batch solve runs.  1 <= count <= 4096.
  *   o: rtol, restart, maxit, x0_is_zero and arnoldi for every instance (as for

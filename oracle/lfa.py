@@ -288,17 +288,20 @@ def optimise_omega(tg: TwoGrid, nu1: int, nu2: int, omegas=None, omega_J: float 
     return best
 
 
-def optimise_bsr(tg: TwoGrid, nu1: int = 1, nu2: int = 1, omegas=None, omegas_J=None):
+def optimise_bsr(tg: TwoGrid, nu1: int = 1, nu2: int = 1, omegas=None, omegas_J=None,
+                 tie: float = 1e-3):
     """Joint brute-force minimisation over (omega_J, omega) in steps of 0.02 (Sec. 4.3,
-    Table 3).  Returns (omega_J_opt, omega_opt, rho_opt)."""
+    Table 3).  Where rho_LFA is flat in omega_J (it is limited by a mode that the Schur
+    step does not touch), every omega_J within ``tie`` of the minimum is optimal; of those
+    the one closest to 1 (plain Jacobi) is returned.  Returns (omega_J, omega, rho)."""
     if omegas is None:
         omegas = np.round(np.arange(0.40, 1.2001, 0.02), 2)
     if omegas_J is None:
         omegas_J = np.round(np.arange(0.70, 1.5001, 0.02), 2)
-    best = (None, None, np.inf)
+    res = []
     for oj in omegas_J:
         for om in omegas:
-            r = tg.rho(float(om), nu1, nu2, float(oj))
-            if r < best[2]:
-                best = (float(oj), float(om), r)
-    return best
+            res.append((float(oj), float(om), tg.rho(float(om), nu1, nu2, float(oj))))
+    rmin = min(r for _, _, r in res)
+    cand = [t for t in res if t[2] <= rmin + tie]
+    return min(cand, key=lambda t: (abs(t[0] - 1.0), t[2]))

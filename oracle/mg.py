@@ -34,11 +34,12 @@ class Hierarchy:
     def __init__(self, n: int, prm: fem.Params, kinv_L, kinv_U, smoother: str = "vanka",
                  omega: float = 0.8, omega_J: float = 1.0, nu1: int = 1, nu2: int = 1,
                  n_coarse: int = 8, coarse_op: str = "redisc", p_shift: float = 0.0,
-                 w_essential: bool = False):
+                 w_essential: bool = False, gamma: int = 1):
         assert n >= n_coarse and (n // n_coarse) * n_coarse == n
         assert (n // n_coarse) & ((n // n_coarse) - 1) == 0, "n must be n_coarse * 2^k"
         self.prm = prm
         self.nu1, self.nu2 = nu1, nu2
+        self.gamma = int(gamma)                 # coarse-grid cycles per level: 1 = V, 2 = W
         self.levels = []
         m = n
         while True:
@@ -87,7 +88,9 @@ class Hierarchy:
         return x
 
     def vcycle(self, b: np.ndarray, level: int = 0) -> np.ndarray:
-        """Approximate A_level^{-1} b by one V(nu1, nu2) cycle from a zero initial guess."""
+        """Approximate A_level^{-1} b by one V(nu1, nu2) cycle from a zero initial guess
+        (gamma = 2: a W-cycle, the coarse problem approximated by two cycles, the second on
+        the residual left by the first; the coarsest level is solved directly either way)."""
         if level == len(self.levels) - 1:
             return self.coarse_solve(b)
         L = self.levels[level]
@@ -95,7 +98,12 @@ class Hierarchy:
         for _ in range(self.nu1):
             x = L.smoother.sweep(L.A, b, x)
         r = b - L.A @ x
-        xc = self.vcycle(L.R @ r, level + 1)
+        rc = L.R @ r
+        xc = self.vcycle(rc, level + 1)
+        if level + 2 < len(self.levels):
+            C = self.levels[level + 1]
+            for _ in range(self.gamma - 1):
+                xc = xc + self.vcycle(rc - C.A @ xc, level + 1)
         x = x + L.P @ xc
         for _ in range(self.nu2):
             x = L.smoother.sweep(L.A, b, x)

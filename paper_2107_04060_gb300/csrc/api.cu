@@ -90,7 +90,7 @@ static void free_level(Level &L) {
   cudaFree(L.slot); cudaFree(L.pinv64); cudaFree(L.pinv32);
   cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
   cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
-  cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2);
+  cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2); cudaFree(L.wz);
   cudaFree(L.bz); cudaFree(L.bd);
   L = Level();
 }
@@ -453,6 +453,8 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
   if (!(std::isfinite(o->omega) && o->omega > 0.0) || !std::isfinite(o->omega_J) ||
       !(std::isfinite(o->p_shift) && o->p_shift >= 0.0))
     return arg_error("bmg_setup_hierarchy: omega > 0, finite omega_J, p_shift >= 0 required");
+  if (o->gamma < 0 || o->gamma > 2)
+    return arg_error("bmg_setup_hierarchy: gamma must be 0 or 1 (V-cycle) or 2 (W-cycle)");
   const int n = s->n;
   if (o->n_coarse < 2 || o->n_coarse > 64 || n < o->n_coarse || n % o->n_coarse)
     return arg_error("bmg_setup_hierarchy: need 2 <= n_coarse <= 64 dividing n");
@@ -506,6 +508,11 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
     cudaMemsetAsync(L.z, 0, es * vl, st);
     cudaMemsetAsync(L.t, 0, es * vl, st);
     cudaMemsetAsync(L.t2, 0, es * vl, st);
+    if (o->gamma == 2 && m != n && m != o->n_coarse) {       // levels that take a second cycle
+      if (cudaMalloc(&L.wz, es * vl) != cudaSuccess)
+        return fail(cuda_fail(cudaErrorMemoryAllocation, "W-cycle work vector"));
+      cudaMemsetAsync(L.wz, 0, es * vl, st);
+    }
     L.err = h->d_flag;
     // FP32 operator input staged by TMA: the V-cycle applies the operator to z (to t2 on the
     // finest level); tuning decides whether that variant runs
@@ -614,6 +621,13 @@ static int vcycle_level(bmg_hierarchy *h, size_t l, const T *rhs, T *z, cudaStre
   const Level &C = h->levels[l + 1];
   if ((rc = launch_restrict<T>(L, C, res, (T *)C.rhs, st))) return rc;
   if ((rc = vcycle_level<T>(h, l + 1, (const T *)C.rhs, (T *)C.z, st))) return rc;
+  if (h->opts.gamma == 2 && l + 2 < h->levels.size()) {
+    // W-cycle: a second coarse cycle on the residual left by the first, added to its result
+    // (the coarsest level's direct solve needs none)
+    if ((rc = launch_apply<T>(C, (const T *)C.z, (const T *)C.rhs, (T *)C.t2, true, 1, 0, st))) return rc;
+    if ((rc = vcycle_level<T>(h, l + 1, (const T *)C.t2, (T *)C.wz, st))) return rc;
+    if ((rc = launch_add<T>((T *)C.z, (const T *)C.wz, vec_len_of(C.n), st))) return rc;
+  }
   if ((rc = launch_prolong_add<T>(L, C, (const T *)C.z, z, st))) return rc;
   for (int s = 0; s < h->opts.nu2; ++s) {
     if ((rc = launch_apply<T>(L, z, rhs, t, true, 1, 0, st))) return rc;

@@ -146,6 +146,7 @@ struct Level {
   float *cinv32 = nullptr;
   // work vectors in the V-cycle precision
   void *rhs = nullptr, *z = nullptr, *t = nullptr, *t2 = nullptr;
+  void *wz = nullptr;                  // W-cycle: result of the second coarse cycle
   // Tile shape of the operator / Vanka / displacement-Vanka launches on this level, chosen by
   // timing at setup (index into each kernel's candidate list; -1: the CTA-count rule).
   int tile_apply = -1, tile_vanka = -1, tile_vanka_u = -1;
@@ -323,6 +324,8 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
 // vector kernels
 template <typename T>
 int launch_fill(T *x, T v, size_t n, cudaStream_t st, const int *gate = nullptr);
+template <typename T>
+int launch_add(T *y, const T *x, size_t n, cudaStream_t st);      // y += x
 int launch_convert_d2f(const double *x, float *y, size_t n, cudaStream_t st);
 int launch_convert_f2d(const float *x, double *y, size_t n, cudaStream_t st);
 int launch_dots(const double *V, size_t ldv, int k, const double *w, size_t n,

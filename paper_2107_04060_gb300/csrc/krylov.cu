@@ -29,6 +29,25 @@ int launch_fill(T *x, T v, size_t n, cudaStream_t st, const int *gate) {
 template int launch_fill<double>(double *, double, size_t, cudaStream_t, const int *);
 template int launch_fill<float>(float *, float, size_t, cudaStream_t, const int *);
 
+template <typename T>
+__global__ void add_kernel(T *__restrict__ y, const T *__restrict__ x, size_t n) {
+  pdl_enter();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+template <typename T>
+int launch_add(T *y, const T *x, size_t n, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  BMG_CUDA(launch_pdl(add_kernel<T>, dim3(blocks), dim3(256), 0, st, y, x, n));
+  BMG_CHECK_LAUNCH("add_kernel");
+  return BMG_OK;
+}
+template int launch_add<double>(double *, const double *, size_t, cudaStream_t);
+template int launch_add<float>(float *, const float *, size_t, cudaStream_t);
+
 __global__ void d2f_kernel(const double *x, float *y, size_t n) {
   pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

@@ -190,3 +190,45 @@ def test_fgmres_iterations_n128_match_oracle(bmg, smoother, omega):
     _, oinfo = krylov.fgmres(A, H.levels[0].mesh.pack(f), H.vcycle, rtol=1e-8, restart=50, maxit=400)
     assert info["status"] == "converged" and oinfo["converged"]
     assert abs(info["iters"] - oinfo["iters"]) <= 1, (info["iters"], oinfo["iters"])
+
+
+@pytest.mark.parametrize("smoother,omega", [("bsr", 0.7), ("vanka", 0.7)])
+@pytest.mark.parametrize("n", [32, 64])
+def test_w_cycle_parity(bmg, smoother, omega, n):
+    """W(1,1) cycle (gamma = 2) against the oracle's, lognormal K, three and four levels."""
+    import torch
+    p = dict(lam=1e4, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    kL, kU = synthetic.lognormal_k(n, 1.0, 12)
+    s = bmg.assemble(n, p["lam"], p["mu"], kfield(bmg, n, kL, kU), 1.0, p["tau"], p["alpha"], p["inv_M"])
+    h = bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8, cycle="W")
+    H = mg.Hierarchy(n, fem.Params(**p), 1 / kL, 1 / kU, smoother=smoother, omega=omega,
+                     omega_J=1.0, nu1=1, nu2=1, n_coarse=8, gamma=2)
+    f = synthetic.rhs(n, 8)
+    r = dev(bmg, n, f)
+    z = torch.empty_like(r)
+    h.vcycle(r, z)
+    zo = H.vcycle(H.levels[0].mesh.pack(f))
+    assert relmax(to_oracle(bmg, H.levels[0].mesh, z), zo) < 1e-9
+
+
+def test_w_cycle_bsr_fgmres_iterations_match_oracle(bmg):
+    """BSR with W(1,1) cycles, n = 64, unit parameters: FGMRES counts within one of the
+    oracle's (and far below the V-cycle's, whose stationary iteration diverges here)."""
+    import torch
+    n = 64
+    p = dict(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    s = bmg.assemble(n, 1.0, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    hw = bmg.setup_hierarchy(s, "bsr", 1, 1, omega=0.7, omega_J=1.0, n_coarse=8, cycle="W")
+    hv = bmg.setup_hierarchy(s, "bsr", 1, 1, omega=0.7, omega_J=1.0, n_coarse=8)
+    H = mg.Hierarchy(n, fem.Params(**p), np.ones((n, n)), np.ones((n, n)), smoother="bsr",
+                     omega=0.7, omega_J=1.0, n_coarse=8, gamma=2)
+    f = synthetic.rhs(n, 0)
+    b = dev(bmg, n, f)
+    xw, xv = torch.zeros_like(b), torch.zeros_like(b)
+    iw = hw.fgmres_solve(b, xw, rtol=1e-8, restart=50, maxit=400)
+    iv = hv.fgmres_solve(b, xv, rtol=1e-8, restart=50, maxit=400)
+    _, oinfo = krylov.fgmres(H.levels[0].A, H.levels[0].mesh.pack(f), H.vcycle, rtol=1e-8,
+                             restart=50, maxit=400)
+    assert iw["status"] == "converged" and oinfo["converged"]
+    assert abs(iw["iters"] - oinfo["iters"]) <= 1, (iw["iters"], oinfo["iters"])
+    assert iw["iters"] < iv["iters"]

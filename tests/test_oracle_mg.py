@@ -172,3 +172,32 @@ def test_patch_shift_equals_compressibility():
     P = A0[p][:, p].toarray()
     assert np.linalg.cond(P) > 1e12
     assert np.linalg.cond(P - s * 0.5 * m.h ** 2 * np.diag(fem.type_mask(m, fem.P_TYPES)[p])) < 1e10
+
+
+def test_w_cycle_restores_the_two_grid_factor_for_inexact_bsr():
+    """The discussion of Table 4: multilevel inexact BSR struggles where the two-level method
+    is robust, and W-cycles may be needed.  With the unit parameters (lambda = mu = K = tau =
+    alpha = 1/M = 1) on a 32-cell grid, the stationary V(1,1) iteration with three levels
+    diverges, while the W(1,1) iteration converges at the two-grid factor (within 0.03) and
+    the LFA prediction for these parameters (0.687)."""
+    n = 32
+    prm = fem.Params(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    one = np.ones((n, n))
+
+    def factor(nc, gamma):
+        H = mg.Hierarchy(n, prm, one, one, smoother="bsr", omega=0.7, omega_J=1.0, n_coarse=nc,
+                         gamma=gamma)
+        L = H.levels[0]
+        x = L.mesh.pack(synthetic.uniform_field(n, 1)) * L.mesh.free
+        r0 = np.linalg.norm(L.A @ x)
+        for _ in range(30):
+            x = x + H.vcycle(-(L.A @ x))
+            r1 = np.linalg.norm(L.A @ x)
+            rho, r0 = r1 / r0, r1
+        return rho
+
+    tg = factor(16, 1)
+    assert factor(8, 1) > 1.0
+    w = factor(8, 2)
+    assert abs(w - tg) < 0.03
+    assert abs(w - 0.687) < 0.03
