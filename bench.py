@@ -44,10 +44,11 @@ MAXIT = 1000
 # roofline denominators: FP64 FMA pipe (nominal 1.25 TFLOP/s for the GB300; measured
 # 1.20 TFLOP/s with a register FMA loop), HBM from the measured-peaks file of this GPU model
 FP64_PEAK_TFLOPS = 1.25
-# DRAM bytes per fine-level launch of the FP64 operator inside the sweep, from the ncu
-# capture summarised in profiles/apply_fp64_512_sweep_full.md (cell-pair kernel with the
-# reduced halo; null it when the kernel changes)
-APPLY_TRAFFIC_BYTES = 42.8e6
+# DRAM bytes (read + write) per fine-level launch of the FP64 operator inside the sweep, from
+# one ncu capture of the cell-pair kernel, and the SHA-256 prefix of the operator source it
+# was taken with: the bench reports the figure only while that source is unchanged (else
+# null, until the counters are taken again)
+APPLY_TRAFFIC = (42.8e6, "e9b9ef77e8028520")
 # algorithmic work per grid cell of the fine-level kernels: the operator counts the nonzero
 # products of the element matrices (156 flops per triangle, two triangles per cell, plus 26
 # for the gather and the residual); Vanka: the 20 x 20 inverse (400 FMAs) plus the weighted
@@ -55,6 +56,18 @@ APPLY_TRAFFIC_BYTES = 42.8e6
 FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 64 + 10,
                   "restrict": 0, "prolong": 0}
 BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208, "restrict": 100, "prolong": 180}
+
+
+def apply_traffic():
+    """The recorded DRAM bytes per operator launch if the operator source still matches."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2107_04060_gb300", "csrc", "operator.cu")
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return APPLY_TRAFFIC[0] if digest == APPLY_TRAFFIC[1] else None
 
 
 def smoother_cases(inv_M: float = INV_M):
@@ -275,8 +288,12 @@ def run_micro(args):
     if args.micro != "apply":
         h = bmg.setup_hierarchy(s, args.smoother, 1, 1, omega=0.7, precision=args.precision)
     fam = {"apply": "apply", "vanka": "vanka", "vcycle": args.family or "vanka"}[args.micro]
+    b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 2))).cuda()
+
     def run():
-        if args.micro == "apply":
+        if args.micro == "apply" and args.residual:
+            s.residual(b, x, y)
+        elif args.micro == "apply":
             s.apply(x, y)
         else:
             h.vcycle(x, y)
@@ -295,6 +312,7 @@ def run_micro(args):
     cells = prof["cells"] / max(prof["launches"], 1)
     bpc = BYTES_PER_CELL_F64[fam] * (0.5 if args.precision == "fp32" else 1.0)
     print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision, "uniform_k": args.uniform_k,
+                      "residual": args.residual,
                       "gbs_algorithmic_this_precision": bpc * cells / (avg * 1e-3) / 1e9,
                       "call_ms": ev0.elapsed_time(ev1) / args.reps, "kernel": fam,
                       "kernel_avg_ms": avg, "launches": prof["launches"],
@@ -586,6 +604,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--uniform-k", action="store_true", help="--micro: constant K instead of lognormal")
+    ap.add_argument("--residual", action="store_true", help="--micro apply: r = b - A x instead of y = A x")
     ap.add_argument("--smoother", default="vanka", choices=["vanka", "bsr"], help="--micro vcycle: smoother")
     ap.add_argument("--family", default=None, choices=["apply", "vanka", "vanka_u", "restrict", "prolong"],
                     help="--micro vcycle: kernel family to time (default vanka)")
@@ -666,7 +685,7 @@ def main():
             if prec == "fp32" and ci not in fp32_cases:
                 continue
             hier[prec, ci] = bmg.setup_hierarchy(systems[c["lam"], c["K"]], c["smoother"], 1, 1,
-                                                 omega=c["omega"], omega_J=1.0, n_coarse=8,
+                                                 omega=c["omega"], omega_J=c["omega_J"], n_coarse=8,
                                                  precision=prec)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -826,10 +845,19 @@ def main():
     # the same 12 FP64 solves with the mixed-precision Arnoldi (FP32 first Gram-Schmidt pass,
     # double-float second pass and correction)
     arm_steps = max(1, min(args.steps, 5))
-    msA = None
+    msA = msW = None
     if not args.no_arms:
         one_step("fp64", arnoldi="mixed")
         msA, recsA, _, _ = timed("fp64", arm_steps, arnoldi="mixed")
+        # the 6 BSR solves with W(1,1) cycles against the same 6 with V(1,1) cycles
+        bcases = [ci for ci, c in enumerate(cases) if c["smoother"] == "bsr"]
+        hierW = {("fp64", ci): bmg.setup_hierarchy(systems[cases[ci]["lam"], cases[ci]["K"]], "bsr", 1, 1,
+                                                   omega=cases[ci]["omega"], omega_J=cases[ci]["omega_J"],
+                                                   n_coarse=8, cycle="W") for ci in bcases}
+        one_step("fp64", subset=bcases, hset=hierW)
+        msW, recsW, _, _ = timed("fp64", arm_steps, subset=bcases, hset=hierW)
+        msV, recsV, _, _ = timed("fp64", arm_steps, subset=bcases)
+        del hierW
     stop.set()
     th.join(timeout=5)
     clocks = summarize_clocks(samples)
@@ -908,7 +936,7 @@ def main():
         out["roofline"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
                            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS,
-                           "traffic": APPLY_TRAFFIC_BYTES if dominant == "apply" else None,
+                           "traffic": apply_traffic() if dominant == "apply" else None,
                            "avg_launch_ms": avg_ms, "launches": prof["launches"],
                            "peak_source": "nominal FP64 rate of the GB300 (1.25 TFLOP/s; a register-FMA loop measured 1.20)",
                            "timed_region": f"{nstreams} concurrent solves: launches share the GPU",
@@ -928,6 +956,15 @@ def main():
                         "a double-float second pass and correction",
             "value": work_dofs / (msA * 1e-3) / 1e6, "unit": "MDOF/s", "ms_per_step": msA, "steps": arm_steps,
             "iters": iA, "iter_delta_vs_fp64": [a - b for a, b in zip(iA, i64)]}
+    if msW is not None:
+        bdofs = len(bcases) * nfree * world
+        out["bsr_w_cycle"] = {
+            "workload": "the 6 BSR solves of the sweep with W(1,1) cycles (the remedy for multilevel inexact "
+                        "BSR that the discussion of Table 4 suggests) against the same 6 with V(1,1)",
+            "value": bdofs / (msW * 1e-3) / 1e6, "unit": "MDOF/s", "ms_per_step": msW, "steps": arm_steps,
+            "iters": [r[1]["iters"] for r in recsW[:len(bcases)]],
+            "v_cycle": {"value": bdofs / (msV * 1e-3) / 1e6, "ms_per_step": msV,
+                        "iters": [r[1]["iters"] for r in recsV[:len(bcases)]]}}
     # the sweep at the paper's compressibility group: (1/M) mu / alpha^2 = 1e-2
     if not args.no_arms:
         for key in [k for k in hier if k[0] == "fp32"]:

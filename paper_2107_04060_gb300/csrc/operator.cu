@@ -12,6 +12,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <utility>
@@ -330,21 +331,25 @@ __global__ void __launch_bounds__(NT) apply_batch_kernel(const ApplyArgs<double>
 // counts the bytes; every thread waits on it (bounded: after the limit the CTA sets the
 // level's error flag, waits once more for its copies and leaves).  Phases 1 and 2 are
 // apply_tile's, reading the slab instead of global memory.
+constexpr int kTmaTX = 32, kTmaTY = 8, kTmaNT = 256, kTmaBX = 40, kTmaBY = kTmaTY + 2;
+constexpr long long kTmaWaitLimit = 1ll << 22;
+
 struct TmaMaps {
   const void *xptr[2] = {nullptr, nullptr};
   CUtensorMap x[2];
   CUtensorMap coef;
+  // iteration limit of the first wait on the copies (the environment variable
+  // BMG_DEBUG_TMA_WAIT_LIMIT lowers it at setup, so that a test can make the wait run out;
+  // the second wait, for the copies still in flight, keeps the full limit)
+  long long wait_limit = kTmaWaitLimit;
 };
-
-constexpr int kTmaTX = 32, kTmaTY = 8, kTmaNT = 256, kTmaBX = 40, kTmaBY = kTmaTY + 2;
-constexpr long long kTmaWaitLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < kTmaWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -375,7 +380,7 @@ template <int WM>
 __global__ void __launch_bounds__(kTmaNT) apply_tma_kernel(const __grid_constant__ ApplyArgs<float> a,
                                                            const __grid_constant__ CUtensorMap tx,
                                                            const __grid_constant__ CUtensorMap tc,
-                                                           int *err) {
+                                                           int *err, long long wait_limit) {
   constexpr int NC = WM ? 12 : 2;
   constexpr uint32_t kBytes = sizeof(float) * (10 * kTmaBY * kTmaBX + NC * (kTmaBY - 1) * kTmaBX);
   pdl_enter();
@@ -401,10 +406,10 @@ __global__ void __launch_bounds__(kTmaNT) apply_tma_kernel(const __grid_constant
     tma_load_3d(smem_u32(xs), &tx, x0, y0, 0, b);
     tma_load_3d(smem_u32(cs), &tc, x0, y0, 0, b);
   }
-  const bool ok = mbar_wait_bounded(b, 0);
+  const bool ok = mbar_wait_bounded(b, 0, wait_limit);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicOr(err, kErrTmaTimeout);
-    mbar_wait_bounded(b, 0);
+    mbar_wait_bounded(b, 0, kTmaWaitLimit);          // let the copies in flight land
     return;
   }
   const SmemSrc<kTmaBX, kTmaBY> src{xs, cs, x0, y0};
@@ -421,7 +426,8 @@ static int launch_apply_tma(const ApplyArgs<float> &a, const Level &L, const CUt
     attr = true;
   }
   dim3 grid((L.g.pitch + kTmaTX - 1) / kTmaTX, (L.n + 1 + kTmaTY - 1) / kTmaTY);
-  BMG_CUDA(launch_pdl(apply_tma_kernel<WM>, grid, dim3(kTmaNT), smem, st, a, tx, L.tma->coef, L.err));
+  BMG_CUDA(launch_pdl(apply_tma_kernel<WM>, grid, dim3(kTmaNT), smem, st, a, tx, L.tma->coef, L.err,
+                      L.tma->wait_limit));
   return BMG_OK;
 }
 
@@ -458,6 +464,10 @@ int setup_apply_tma(Level &L, const float *xa, const float *xb) {
   const float *coef = L.wm_full ? L.wm32 : L.kinv32;
   if (!coef || L.n < kTmaTX) return BMG_OK;
   TmaMaps *t = new TmaMaps();
+  if (const char *lim = std::getenv("BMG_DEBUG_TMA_WAIT_LIMIT")) {
+    const long long v = std::atoll(lim);
+    if (*lim && v >= 0 && v < kTmaWaitLimit) t->wait_limit = v;
+  }
   bool ok = encode_planes(&t->coef, coef, L.g.pitch, L.n + 1, L.wm_full ? 12 : 2, L.g.blk, kTmaBY - 1);
   const float *xs[2] = {xa, xb};
   for (int k = 0; k < 2 && ok; ++k) {

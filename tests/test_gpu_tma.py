@@ -53,3 +53,30 @@ def test_tma_operator_matches_global_loads_bitwise(lognormal):
     i0 = h0.fgmres_solve(b, x0, rtol=1e-8, maxit=300)
     assert i5["status"] == "converged" and i5["iters"] == i0["iters"]
     assert torch.equal(x5, x0)
+
+
+def test_bounded_tma_wait_reports_timeout_without_fault():
+    """The wait of the TMA-staged FP32 operator on its bulk copies is bounded.  With the first
+    wait's limit lowered to zero spins at setup (BMG_DEBUG_TMA_WAIT_LIMIT=0), every CTA gives
+    up at once, records the timeout in the hierarchy's error flag, waits with the full limit
+    for its own copies to land and returns: the solve reports BMG_ERR_CUDA with the reason,
+    nothing faults, and the device stays usable."""
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    torch.cuda.set_device(0)
+    n = 64
+    os.environ["BMG_DEBUG_TMA_WAIT_LIMIT"] = "0"
+    try:
+        s, h = _hierarchy(bmg, torch, n, None, 5)
+    finally:
+        del os.environ["BMG_DEBUG_TMA_WAIT_LIMIT"]
+    assert h.tile(0, "apply") == 5                     # the TMA variant is in use
+    b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).cuda()
+    x = torch.zeros_like(b)
+    with pytest.raises(bmg.BmgError, match="CUDA error.*bulk-copy wait"):
+        h.fgmres_solve(b, x, rtol=1e-8, maxit=3)
+    torch.cuda.synchronize()                             # no sticky error: the context is fine
+    s2, h2 = _hierarchy(bmg, torch, n, None, 5)
+    x2 = torch.zeros_like(b)
+    info = h2.fgmres_solve(b, x2, rtol=1e-8, maxit=300)
+    assert info["status"] == "converged"
