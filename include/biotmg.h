@@ -74,6 +74,8 @@ extern "C" {
 #define BMG_BSR 1             /* inexact Braess-Sarazin (Sec. 3.2.2, App. D)            */
 #define BMG_FP64 0
 #define BMG_FP32 1
+#define BMG_REDISC 0          /* coarse operators by rediscretisation (Sec. 3, the paper's) */
+#define BMG_GALERKIN 1        /* coarse operators P^T A P (R = P^T, Eq. block_interp)      */
 
 typedef struct bmg_system bmg_system;       /* one assembled operator (FP64)           */
 typedef struct bmg_hierarchy bmg_hierarchy; /* multigrid preconditioner for a system   */
@@ -134,12 +136,19 @@ typedef struct {
                        (the remedy the discussion of Table 4 suggests for multilevel inexact
                        BSR): the coarse problem is approximated by two cycles, the second on
                        the residual the first leaves; the coarsest solve is direct either way */
+  int coarse_op;    /* BMG_REDISC (0) or BMG_GALERKIN: P^T A P on every coarse level.  P_u is
+                       local to each coarse triangle, so P^T A P is an element assembly: the
+                       coarse elasticity element matrices become dense 9 x 9 products, the
+                       grad-div block is exactly 4 x its rediscretisation per level (the whole
+                       divergence of a coarse triangle lands in its interior child), and the
+                       RT0 and P0 blocks equal their rediscretisation (nested spaces)        */
 } bmg_mg_opts;
 
 /*
  * bmg_setup_hierarchy -- multigrid hierarchy for system s (Sec. 3): levels n, n/2, ...,
- * n_coarse with rediscretised operators (the coarse RT0 mass is P_w^T M_w P_w, which is
- * the rediscretisation with the fine-scale K^{-1}); FP64 factorisation of every distinct
+ * n_coarse with rediscretised (or, with coarse_op = BMG_GALERKIN, Galerkin) operators (the
+ * coarse RT0 mass is P_w^T M_w P_w, which is the rediscretisation with the fine-scale
+ * K^{-1}); FP64 factorisation of every distinct
  * Vanka patch matrix (Gauss-Jordan with partial pivoting); FP64 inverse of the coarsest
  * operator.  The hierarchy keeps a pointer to s: s must outlive it.
  * Errors: BMG_ERR_ARG (n not n_coarse * 2^k, bad options), BMG_ERR_SINGULAR, BMG_ERR_ALLOC,
@@ -271,8 +280,8 @@ size_t bmg_noalloc_capacity(void);
  *
  * bmg_batch_create(hs, count, o, autotune, stream, out)
  *   hs[count]: distinct hierarchies from bmg_setup_hierarchy, all with smoother BMG_VANKA,
- *     precision BMG_FP64, V-cycles (gamma 0 or 1), nu1 >= 1 and the same nu1, nu2 and
- *     n_coarse (omega may differ).
+ *     precision BMG_FP64, V-cycles (gamma 0 or 1), rediscretised coarse operators, nu1 >= 1
+ *     and the same nu1, nu2 and n_coarse (omega may differ).
  *     The batch borrows their level data and work vectors: keep them alive, and do not use
  *     them in other solves while a batch solve runs.  1 <= count <= 4096.
  *   o: rtol, restart, maxit, x0_is_zero and arnoldi for every instance (as for

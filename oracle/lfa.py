@@ -43,8 +43,8 @@ condition reaches.
     spaced points offset so that none is at the origin (Sec. 4.3).
 
 Pinned by: the rho_LFA and omega_opt printed in Table 2 (Vanka V(2,2)) and Table 3 (inexact
-BSR V(1,1)), and the nested Galerkin identity R~ (tau M_w)~ P~ = (tau M_w)~_2h of the RT0
-block (tests/test_oracle_lfa.py).
+BSR V(1,1)), the nested Galerkin identities of the RT0 and P0 blocks, and the projection
+property of the Galerkin coarse-grid correction (tests/test_oracle_lfa.py).
 """
 from __future__ import annotations
 
@@ -177,11 +177,13 @@ def vanka_entries(prm: fem.Params, kinv: float, h: float, with_flow: bool = True
 class TwoGrid:
     """Two-grid LFA of the monolithic method for one parameter set (constant K = k I).
 
-    ``smoother`` is "vanka" or "bsr".  The damping-independent symbols are formed once at
-    the sample frequencies; ``rho(omega, nu1, nu2, omega_J)`` evaluates rho_LFA."""
+    ``smoother`` is "vanka" or "bsr"; ``coarse`` is "redisc" (the rediscretised coarse
+    operator, Sec. 3) or "galerkin" (its symbol R~ A~ P~).  The damping-independent symbols
+    are formed once at the sample frequencies; ``rho(omega, nu1, nu2, omega_J)`` evaluates
+    rho_LFA."""
 
     def __init__(self, prm: fem.Params, k: float, h: float, smoother: str = "vanka",
-                 samples: int = 32):
+                 samples: int = 32, coarse: str = "redisc"):
         self.prm = prm
         self.smoother = smoother
         self.theta = low_frequencies(samples)
@@ -204,6 +206,10 @@ class TwoGrid:
             Rb[:, :, a * NT:(a + 1) * NT] = self.R[a]
         Pb = np.conj(np.transpose(Rb, (0, 2, 1))) / 4.0
         self.Lb, self.Rb, self.Pb = Lb, Rb, Pb
+        if coarse == "galerkin":
+            self.AH = Rb @ Lb @ Pb
+        elif coarse != "redisc":
+            raise ValueError(coarse)
         self.cgc = np.eye(4 * NT)[None] - Pb @ np.linalg.solve(self.AH, Rb @ Lb)
         if smoother == "vanka":
             self._minv = [vanka_entries(prm, kinv, h).symbol(self.theta + np.pi * np.asarray(a, float))

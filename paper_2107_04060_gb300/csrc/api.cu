@@ -455,6 +455,8 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
     return arg_error("bmg_setup_hierarchy: omega > 0, finite omega_J, p_shift >= 0 required");
   if (o->gamma < 0 || o->gamma > 2)
     return arg_error("bmg_setup_hierarchy: gamma must be 0 or 1 (V-cycle) or 2 (W-cycle)");
+  if (o->coarse_op != BMG_REDISC && o->coarse_op != BMG_GALERKIN)
+    return arg_error("bmg_setup_hierarchy: coarse_op must be BMG_REDISC or BMG_GALERKIN");
   const int n = s->n;
   if (o->n_coarse < 2 || o->n_coarse > 64 || n < o->n_coarse || n % o->n_coarse)
     return arg_error("bmg_setup_hierarchy: need 2 <= n_coarse <= 64 dividing n");
@@ -491,6 +493,10 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
       int rc = alloc_coefs(L, L.wm_full);
       if (rc) return fail(rc);
       make_coefs(s->prm, m, &L.c64, &L.c32);
+      if (o->coarse_op == BMG_GALERKIN) {
+        galerkin_coarsen_coefs(h->levels[h->levels.size() - 2].c64, &L.c64, &L.c32);
+        L.dense_a = true;
+      }
       if (s->uniform) {
         if ((rc = launch_fill<double>(L.kinv64, 1.0 / s->K_const, 2 * L.g.blk, st)) ||
             (rc = launch_fill<float>(L.kinv32, (float)(1.0 / s->K_const), 2 * L.g.blk, st)))

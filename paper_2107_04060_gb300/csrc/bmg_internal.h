@@ -79,6 +79,10 @@ struct PhysParams {
 };
 
 void make_coefs(const PhysParams &p, int n, OpCoefs<double> *c64, OpCoefs<float> *c32);
+// Galerkin coarse coefficients: c64 / c32 hold the rediscretised coefficients of the coarse
+// level on entry; the displacement block is replaced by the Galerkin product of the fine
+// level's (dense elasticity element matrices, fine lambda / |T|).
+void galerkin_coarsen_coefs(const OpCoefs<double> &fine, OpCoefs<double> *c64, OpCoefs<float> *c32);
 
 // --------------------------------------------------------------------------------------
 // Transfer stencil tables (pure geometry; identical on every level).
@@ -115,6 +119,7 @@ struct Level {
   Grid g{};
   bool wm_full = false;        // per-triangle 3x3 RT0 mass (coarse levels, varying K)
   bool uniform = false;        // every triangle has the same coefficients
+  bool dense_a = false;        // Galerkin coarse level: dense elasticity element matrices
   double *kinv64 = nullptr;    // [2][blk] per-triangle K^{-1} (wm_full == false)
   float *kinv32 = nullptr;
   double *wm64 = nullptr;      // [2][6][blk] symmetric 3x3 RT0 mass incl. tau (wm_full)

@@ -363,7 +363,77 @@ void local_prolongation(int o, int I, int J, SparseP &P) {
   }
 }
 
+// The four children of coarse triangle (o, I, J) in fine grid units, corner at A_k first,
+// the interior child last (the order of local_prolongation).
+void coarse_children(int o, int I, int J, int child[4][3][2]) {
+  int cv[3][2];
+  tri_vertices(o, I, J, cv);
+  int A[3][2], M[3][2];
+  for (int k = 0; k < 3; ++k) { A[k][0] = 2 * cv[k][0]; A[k][1] = 2 * cv[k][1]; }
+  for (int k = 0; k < 3; ++k) {
+    int a = (k + 1) % 3, b = (k + 2) % 3;
+    M[k][0] = (A[a][0] + A[b][0]) / 2;
+    M[k][1] = (A[a][1] + A[b][1]) / 2;
+  }
+  const int *pts[4][3] = {{A[0], M[2], M[1]}, {A[1], M[0], M[2]}, {A[2], M[1], M[0]}, {M[0], M[1], M[2]}};
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < 3; ++k) { child[c][k][0] = pts[c][k][0]; child[c][k][1] = pts[c][k][1]; }
+}
+
 }  // namespace
+
+// Galerkin displacement block of the next coarser level (Sec. 3, R = P^T: the coarse
+// operator P^T A P in place of the rediscretisation).  P_u is local to each coarse triangle
+// T: every fine displacement DoF inside T or on its edges is a combination of T's nine
+// coarse displacement DoFs (point values, half-edge bubbles and the zero-flux corner
+// bubbles of Sec. 3.1 all use T's data only).  Hence P_u^T A_u P_u is again an element
+// assembly, with element matrices E_T = sum over the four children t of Q_t^T E_t Q_t,
+// Q_t the 9 x 9 map from T's local DoFs to t's.  For the elasticity part this gives a dense
+// 9 x 9 matrix (Af -> Ac below).  The grad-div part needs no product: B_u,h P_u puts the
+// whole divergence of T into its interior child, so P_u^T (lambda B_u^T M_p^{-1} B_u)_h P_u is
+// 4 lambda (B_u^T M_p^{-1} B_u)_H exactly, i.e. lambda / |T| keeps its fine-level value.  The
+// other blocks of P^T A P equal the rediscretised ones (nested RT0 and P0 spaces).
+void galerkin_elasticity(const double Af[2][81], double Ac[2][81]) {
+  for (int o = 0; o < 2; ++o) {
+    const int I = 1, J = 1;
+    SparseP P;
+    local_prolongation(o, I, J, P);
+    int child[4][3][2];
+    coarse_children(o, I, J, child);
+    double E[9][9] = {};
+    for (int c = 0; c < 4; ++c) {
+      int co, ci, cj;
+      tri_of(child[c], &co, &ci, &cj);
+      double Q[9][9];
+      for (int b = 0; b < 9; ++b) {
+        auto row = P.find(tri_dof(co, ci, cj, b));
+        for (int a = 0; a < 9; ++a) {
+          Q[b][a] = 0.0;
+          if (row == P.end()) continue;
+          auto it = row->second.find(tri_dof(o, I, J, a));
+          if (it != row->second.end()) Q[b][a] = it->second;
+        }
+      }
+      for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b) {
+          double acc = 0.0;
+          for (int r = 0; r < 9; ++r)
+            for (int q = 0; q < 9; ++q) acc += Q[r][a] * Af[co][r * 9 + q] * Q[q][b];
+          E[a][b] += acc;
+        }
+    }
+    for (int a = 0; a < 9; ++a)
+      for (int b = 0; b < 9; ++b) Ac[o][a * 9 + b] = 0.5 * (E[a][b] + E[b][a]);
+  }
+}
+
+void galerkin_coarsen_coefs(const OpCoefs<double> &fine, OpCoefs<double> *c64, OpCoefs<float> *c32) {
+  galerkin_elasticity(fine.A, c64->A);
+  c64->lam_area = fine.lam_area;
+  for (int o = 0; o < 2; ++o)
+    for (int k = 0; k < 81; ++k) c32->A[o][k] = (float)c64->A[o][k];
+  c32->lam_area = (float)c64->lam_area;
+}
 
 void build_transfer_tables(TransferTables *t) {
   std::memset(t, 0, sizeof(*t));

@@ -59,7 +59,7 @@ __host__ __device__ constexpr bool rows_need_s() {
   return need;
 }
 
-template <typename T, int WM, unsigned ROWS>
+template <typename T, int WM, unsigned ROWS, bool DENSE = false>
 __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T u[9],
                                             const T w[3], T p, T kinv, const T *wmT,
                                             T *yl) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void tri_product(const OpCoefs<T> &c, int o, const T 
       if constexpr (g_nonzero(a)) acc = fma(c.g[o][a], s, acc);
       static_for<9>([&](auto b_) {
         constexpr int b = decltype(b_)::value;
-        if constexpr (aeps_nonzero(a, b)) acc = fma(c.A[o][a * 9 + b], u[b], acc);
+        if constexpr (DENSE || aeps_nonzero(a, b)) acc = fma(c.A[o][a * 9 + b], u[b], acc);
       });
       yl[a] = acc;
     }
@@ -157,7 +157,7 @@ struct SmemSrc {                 // slab: x [10][BY][BX], coefficients [NC][BY -
 // LROWS / UROWS select the rows of each triangle that are formed (halo cells need a few).
 constexpr int kCellSlots = 20;
 
-template <typename T, int WM, unsigned LROWS, unsigned UROWS, typename Src>
+template <typename T, int WM, unsigned LROWS, unsigned UROWS, bool DENSE, typename Src>
 __device__ __forceinline__ void cell_product(const OpCoefs<T> &c, const Src &src, int ci, int cj, int n,
                                              T *slot) {
   if (ci < 0 || cj < 0 || ci >= n || cj >= n) {
@@ -195,7 +195,7 @@ __device__ __forceinline__ void cell_product(const OpCoefs<T> &c, const Src &src
   {
     const T u[9] = {ux00, ux10, ux01, uy00, uy10, uy01, bd, bvL, bhL};
     const T w[3] = {wd, wvL, whL};
-    tri_product<T, WM, LROWS>(c, 0, u, w, src.xv(PL, ci, cj), kin[0], wm[0], yl);
+    tri_product<T, WM, LROWS, DENSE>(c, 0, u, w, src.xv(PL, ci, cj), kin[0], wm[0], yl);
   }
   slot[0] = yl[0]; slot[1] = yl[3]; slot[2] = yl[7]; slot[3] = yl[8];
   slot[4] = yl[10]; slot[5] = yl[11]; slot[6] = yl[12];
@@ -206,7 +206,7 @@ __device__ __forceinline__ void cell_product(const OpCoefs<T> &c, const Src &src
   {
     const T u[9] = {ux11, ux01, ux10, uy11, uy01, uy10, bd, bvU, bhU};
     const T w[3] = {wd, wvU, whU};
-    tri_product<T, WM, UROWS>(c, 1, u, w, src.xv(PU, ci, cj), kin[1], wm[1], yu);
+    tri_product<T, WM, UROWS, DENSE>(c, 1, u, w, src.xv(PU, ci, cj), kin[1], wm[1], yu);
   }
   slot[7] = yu[2]; slot[8] = yu[5]; slot[9] = yu[1]; slot[10] = yu[4]; slot[11] = yu[6];
   slot[12] = yu[9]; slot[13] = yu[0]; slot[14] = yu[3]; slot[15] = yu[7]; slot[16] = yu[8];
@@ -229,7 +229,7 @@ __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 // Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
 // tiles on the coarse levels so that their work spreads over many SMs).  sy: shared scratch
 // of kCellSlots values per cell of the tile and of its one-cell halo on the low side.
-template <typename T, int WM, int kTX, int kTY, int NT, typename Src>
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, typename Src>
 __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src, T (*sy)[kCellSlots], int bx,
                                            int by, size_t boff) {
   constexpr int kEX = kTX + 1;
@@ -253,16 +253,16 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
   // the rows the tile gathers
   if (tid < kOwn) {
     const int ci = i0 + tid % kTX, cj = j0 + tid / kTX;
-    cell_product<T, WM, kAllRows, kAllRows>(a.c, src, ci, cj, n, S(ci, cj));
+    cell_product<T, WM, kAllRows, kAllRows, DENSE>(a.c, src, ci, cj, n, S(ci, cj));
   }
   if (tid >= kH0 && tid < kH0 + kTX) {
     const int ci = i0 + (tid - kH0), cj = j0 - 1;
-    cell_product<T, WM, kBottomL, kBottomU>(a.c, src, ci, cj, n, S(ci, cj));
+    cell_product<T, WM, kBottomL, kBottomU, DENSE>(a.c, src, ci, cj, n, S(ci, cj));
   } else if (tid >= kHL && tid < kHL + kTY) {
     const int ci = i0 - 1, cj = j0 + (tid - kHL);
-    cell_product<T, WM, kLeftL, kLeftU>(a.c, src, ci, cj, n, S(ci, cj));
+    cell_product<T, WM, kLeftL, kLeftU, DENSE>(a.c, src, ci, cj, n, S(ci, cj));
   } else if (tid == kHC) {
-    cell_product<T, WM, 0u, kCornerU>(a.c, src, i0 - 1, j0 - 1, n, S(i0 - 1, j0 - 1));
+    cell_product<T, WM, 0u, kCornerU, DENSE>(a.c, src, i0 - 1, j0 - 1, n, S(i0 - 1, j0 - 1));
   }
   __syncthreads();
 
@@ -298,14 +298,15 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
   }
 }
 
-template <typename T, int WM, int kTX, int kTY, int NT>
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE>
 __global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
   pdl_enter();
   BMG_GATE(a.gate);
   extern __shared__ unsigned char smem_raw[];
   const size_t boff = (size_t)blockIdx.z * a.bstride;
   const GlobalSrc<T> src{a.x + boff, a.kinv, a.wm, a.g.blk, a.g.pitch};
-  apply_tile<T, WM, kTX, kTY, NT>(a, src, reinterpret_cast<T(*)[kCellSlots]>(smem_raw), blockIdx.x, blockIdx.y, boff);
+  apply_tile<T, WM, kTX, kTY, NT, DENSE>(a, src, reinterpret_cast<T(*)[kCellSlots]>(smem_raw), blockIdx.x,
+                                        blockIdx.y, boff);
 }
 
 // Batched form: several instances of one grid size in one launch, blockIdx.z selecting the
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(NT) apply_batch_kernel(const ApplyArgs<double>
   extern __shared__ unsigned char smem_raw[];
   double(*sy)[kCellSlots] = reinterpret_cast<double(*)[kCellSlots]>(smem_raw);
   const GlobalSrc<double> src{a.x, a.kinv, a.wm, a.g.blk, a.g.pitch};
-  if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
-  else apply_tile<double, 0, kTX, kTY, NT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+  if (a.wm_full) apply_tile<double, 1, kTX, kTY, NT, false>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+  else apply_tile<double, 0, kTX, kTY, NT, false>(a, src, sy, blockIdx.x, blockIdx.y, 0);
 }
 
 // ---- FP32 operator with TMA-staged input --------------------------------------------------
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kTmaNT) apply_tma_kernel(const __grid_constant
     return;
   }
   const SmemSrc<kTmaBX, kTmaBY> src{xs, cs, x0, y0};
-  apply_tile<float, WM, kTmaTX, kTmaTY, kTmaNT>(a, src, sy, blockIdx.x, blockIdx.y, 0);
+  apply_tile<float, WM, kTmaTX, kTmaTY, kTmaNT, false>(a, src, sy, blockIdx.x, blockIdx.y, 0);
 }
 
 template <int WM>
@@ -485,7 +486,7 @@ void free_apply_tma(Level &L) {
   L.tma = nullptr;
 }
 
-template <typename T, int WM, int TX, int TY, int NT>
+template <typename T, int WM, int TX, int TY, int NT, bool DENSE>
 static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   dim3 block(NT);
   dim3 grid((L.g.pitch + TX - 1) / TX, (L.n + 1 + TY - 1) / TY, batch);
@@ -493,12 +494,12 @@ static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, c
   if (smem > 48 * 1024) {
     static bool attr = false;
     if (!attr) {
-      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT>,
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT, DENSE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr = true;
     }
   }
-  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT>, dim3(grid), dim3(block), smem, st, a));
+  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT, DENSE>, dim3(grid), dim3(block), smem, st, a));
   return BMG_OK;
 }
 
@@ -507,32 +508,32 @@ static long long ctas_for(const Level &L, int tx, int ty, int batch) {
   return (long long)((L.g.pitch + tx - 1) / tx) * ((L.n + 1 + ty - 1) / ty) * batch;
 }
 
-template <typename T, int WM>
+template <typename T, int WM, bool D>
 static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   switch (L.tile_apply) {            // tuned at setup (same candidates as the batched form)
-    case 0: return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
-    case 1: return launch_apply_tile<T, WM, 16, 8, 128>(a, L, batch, st);
-    case 2: return launch_apply_tile<T, WM, 8, 8, 128>(a, L, batch, st);
-    case 3: return launch_apply_tile<T, WM, 8, 4, 96>(a, L, batch, st);
-    case 4: return launch_apply_tile<T, WM, 4, 4, 64>(a, L, batch, st);
+    case 0: return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
+    case 1: return launch_apply_tile<T, WM, 16, 8, 128, D>(a, L, batch, st);
+    case 2: return launch_apply_tile<T, WM, 8, 8, 128, D>(a, L, batch, st);
+    case 3: return launch_apply_tile<T, WM, 8, 4, 96, D>(a, L, batch, st);
+    case 4: return launch_apply_tile<T, WM, 4, 4, 64, D>(a, L, batch, st);
     case 5:                         // FP32, input staged by TMA (else the same 32 x 8 tile)
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (sizeof(T) == 4 && !D) {
         if (L.tma && L.err && batch == 1)
           for (int k = 0; k < 2; ++k)
             if (L.tma->xptr[k] == (const void *)a.x) return launch_apply_tma<WM>(a, L, L.tma->x[k], st);
       }
-      return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
+      return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
     default: break;
   }
   // the largest tile that still gives every SM about two CTAs
   const long long want = 2 * 152;
   // small tiles get more threads than positions so that the triangle products (phase 1)
   // of a tile are spread over more warps
-  if (ctas_for(L, 32, 8, batch) >= want) return launch_apply_tile<T, WM, 32, 8, 256>(a, L, batch, st);
-  if (ctas_for(L, 16, 8, batch) >= want) return launch_apply_tile<T, WM, 16, 8, 128>(a, L, batch, st);
-  if (ctas_for(L, 8, 8, batch) >= want) return launch_apply_tile<T, WM, 8, 8, 128>(a, L, batch, st);
-  if (ctas_for(L, 8, 4, batch) >= want) return launch_apply_tile<T, WM, 8, 4, 96>(a, L, batch, st);
-  return launch_apply_tile<T, WM, 4, 4, 64>(a, L, batch, st);
+  if (ctas_for(L, 32, 8, batch) >= want) return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
+  if (ctas_for(L, 16, 8, batch) >= want) return launch_apply_tile<T, WM, 16, 8, 128, D>(a, L, batch, st);
+  if (ctas_for(L, 8, 8, batch) >= want) return launch_apply_tile<T, WM, 8, 8, 128, D>(a, L, batch, st);
+  if (ctas_for(L, 8, 4, batch) >= want) return launch_apply_tile<T, WM, 8, 4, 96, D>(a, L, batch, st);
+  return launch_apply_tile<T, WM, 4, 4, 64, D>(a, L, batch, st);
 }
 
 template <typename T>
@@ -551,7 +552,9 @@ int launch_apply(const Level &L, const T *x, const T *b, T *y, bool residual, in
   a.wm = (const T *)(f64 ? (const void *)L.wm64 : (const void *)L.wm32);
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
   BMG_PROF_BEGIN(BMG_PROF_APPLY, L.n, st);
-  int rc = L.wm_full ? launch_apply_wm<T, 1>(a, L, batch, st) : launch_apply_wm<T, 0>(a, L, batch, st);
+  // Galerkin coarse levels: dense elasticity element matrices
+  int rc = L.dense_a ? (L.wm_full ? launch_apply_wm<T, 1, true>(a, L, batch, st) : launch_apply_wm<T, 0, true>(a, L, batch, st))
+                     : (L.wm_full ? launch_apply_wm<T, 1, false>(a, L, batch, st) : launch_apply_wm<T, 0, false>(a, L, batch, st));
   BMG_PROF_END(st, (double)L.n * L.n * batch);
   if (rc) return rc;
   BMG_CHECK_LAUNCH("apply_kernel");

@@ -68,3 +68,18 @@ def test_nested_galerkin_identities_of_the_symbols(vanka_04):
     # R_p (-(1/M) M_p) P_p = (-(1/M) M_p)_2h
     g = R[:, p][:, :, rows_p] @ L[:, rows_p][:, :, rows_p] @ P[:, rows_p][:, :, p]
     assert np.abs(g - AH[:, p][:, :, p]).max() <= 1e-12 * np.abs(AH[:, p][:, :, p]).max()
+
+
+def test_galerkin_coarse_grid_correction_is_a_projection_and_rescues_small_inv_m():
+    """With the Galerkin coarse symbol R~ A~ P~ the coarse-grid correction is a projection
+    (spectral radius 1: the coarse-range components are removed exactly, the rest kept).
+    At 1/M = 1e-2 with lambda = mu = K = 1 the rediscretised one amplifies some modes
+    (spectral radius > 1), and V(1,1) additive Vanka converges only with Galerkin."""
+    prm = fem.Params(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1e-2)
+    tr = lfa.TwoGrid(prm, 1.0, 1 / 64, "vanka", samples=16)
+    tg = lfa.TwoGrid(prm, 1.0, 1 / 64, "vanka", samples=16, coarse="galerkin")
+    rho_cgc = lambda t: float(np.abs(np.linalg.eigvals(t.cgc)).max())
+    assert rho_cgc(tg) == pytest.approx(1.0, abs=1e-9)
+    assert rho_cgc(tr) > 2.0
+    assert tr.rho(0.8, 1, 1) > 1.0
+    assert tg.rho(0.8, 1, 1) < 0.85
