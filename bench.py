@@ -71,15 +71,29 @@ def apply_traffic():
     return APPLY_TRAFFIC[0] if digest == APPLY_TRAFFIC[1] else None
 
 
+# Damping of the V(1,1) cycles at each (lambda, K, 1/M) point of the sweep: the minimisers of
+# the two-grid LFA factor (Sec. 4.3 procedure: brute force in steps of 0.02) on the sweep's
+# fine grid, h = 1/512.  Vanka: omega; BSR: (omega_J, omega).
+OMEGA_LFA = {
+    (1.0, 1.0, 1.0): (0.80, 1.08, 0.74), (1.0, 1e-6, 1.0): (0.78, 1.00, 0.82),
+    (1e4, 1.0, 1.0): (0.68, 1.00, 0.68), (1e4, 1e-6, 1.0): (0.68, 1.00, 0.68),
+    (1e6, 1.0, 1.0): (0.68, 1.00, 0.68), (1e6, 1e-6, 1.0): (0.68, 1.00, 0.68),
+    (1.0, 1.0, 1e-2): (0.84, 1.08, 0.74), (1.0, 1e-6, 1e-2): (0.78, 1.00, 0.84),
+    (1e4, 1.0, 1e-2): (0.68, 1.00, 0.68), (1e4, 1e-6, 1e-2): (0.68, 1.00, 0.68),
+    (1e6, 1.0, 1e-2): (0.68, 1.00, 0.68), (1e6, 1e-6, 1e-2): (0.68, 1.00, 0.68),
+}
+
+
 def smoother_cases(inv_M: float = INV_M):
-    """The 12 solves of a sweep step: (lambda, K) pairs with a Vanka and a BSR solve each."""
+    """The 12 solves of a sweep step: (lambda, K) pairs with a Vanka and a BSR solve each,
+    damped as OMEGA_LFA gives."""
     cases = []
     for li, lam in enumerate(LAMBDAS):
         for ki, K in enumerate(KS):
             seed = li * len(KS) + ki
-            cases.append(dict(lam=lam, K=K, seed=seed, smoother="vanka", omega=0.8 if lam == 1.0 else 0.7,
-                              omega_J=1.0))
-            cases.append(dict(lam=lam, K=K, seed=seed, smoother="bsr", omega=0.7, omega_J=1.0))
+            om_v, om_j, om_b = OMEGA_LFA[(lam, K, inv_M)]
+            cases.append(dict(lam=lam, K=K, seed=seed, smoother="vanka", omega=om_v, omega_J=1.0))
+            cases.append(dict(lam=lam, K=K, seed=seed, smoother="bsr", omega=om_b, omega_J=om_j))
     return cases
 
 

@@ -54,7 +54,9 @@ def main(path):
                 print(json.dumps(rec), flush=True)
                 out.append(rec)
     with open(path, "w") as f:
-        json.dump({"source": "two-grid LFA optimum (Sec. 4.3 procedure), oracle/lfa.py",
+        json.dump({"source": "two-grid LFA optimum of the V(1,1) cycle (Sec. 4.3: brute-force sampling "
+                             "of omega in steps of 0.02; Sec. 4.1 Eq. real-TGM; App. C-D), written by "
+                             "oracle/omega_table.py",
                    "points": out}, f, indent=1)
 
 
