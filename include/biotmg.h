@@ -107,6 +107,22 @@ int bmg_assemble(int n, double lambda, double mu, const double *K, double K_cons
                  double tau, double alpha, double inv_M, void *stream, bmg_system **out);
 
 /*
+ * bmg_assemble_divdiv -- as bmg_assemble, choosing the grad-div term: divdiv =
+ * BMG_DIVDIV_REDUCED (0) gives the reduced-quadrature lambda (P_Q div u, P_Q div v) of Sec.
+ * 2.3 (what bmg_assemble builds); BMG_DIVDIV_EXACT gives lambda (div u, div v) integrated
+ * exactly, the original discretisation of Eq. block_form (Sec. 2.1), whose divergence-free
+ * space has no local basis and with which Vanka and inexact Braess-Sarazin relaxation lose
+ * their robustness as lambda / mu grows (Sec. 2.2, Table 1): a negative control.  Every other
+ * call accepts such a system, except bmg_adjoint_gradient and the batched solver
+ * (BMG_ERR_ARG).
+ */
+#define BMG_DIVDIV_REDUCED 0
+#define BMG_DIVDIV_EXACT 1
+int bmg_assemble_divdiv(int n, double lambda, double mu, const double *K, double K_const,
+                        double tau, double alpha, double inv_M, int divdiv, void *stream,
+                        bmg_system **out);
+
+/*
  * bmg_assemble_logk -- as bmg_assemble with the permeability given as its logarithm:
  * logK is a device pointer to FP32 theta_T = log K_T per triangle in the layout of K
  * (K^{-1} = exp(-theta) is formed on the device).  Used by the adjoint gradient below.

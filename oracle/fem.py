@@ -42,14 +42,17 @@ class Params:
     """Physical parameters of one linear solve (one backward-Euler step, Sec. 2.1).
 
     ``inv_M`` is 1/M (the Biot modulus enters only as 1/M); ``mu_f`` is folded into K.
+    ``exact_divdiv`` selects the original discretisation (exact (div u, div v), Sec. 2.1)
+    instead of the reduced-quadrature one (Sec. 2.3).
     """
 
-    def __init__(self, lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1e-6):
+    def __init__(self, lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1e-6, exact_divdiv=False):
         self.lam = float(lam)
         self.mu = float(mu)
         self.tau = float(tau)
         self.alpha = float(alpha)
         self.inv_M = float(inv_M)
+        self.exact_divdiv = bool(exact_divdiv)
 
     @staticmethod
     def from_paper(E: float, nu: float, **kw):
@@ -132,6 +135,7 @@ def element_parts(tri: Triangle):
 
     Returns dict with
       Aeps (9, 9)  int eps(phi_a):eps(phi_b)
+      Ddiv (9, 9)  int div phi_a div phi_b   (exact: the divergence of a bubble is linear)
       g    (9,)    int div phi_a
       Mw   (3, 3)  int psi_a . psi_b
       dw   (3,)    int div psi_a
@@ -139,6 +143,7 @@ def element_parts(tri: Triangle):
     """
     pts, wts = tri.quad()
     Aeps = np.zeros((9, 9))
+    Ddiv = np.zeros((9, 9))
     g = np.zeros(9)
     Mw = np.zeros((3, 3))
     dw = np.zeros(3)
@@ -146,19 +151,26 @@ def element_parts(tri: Triangle):
         _, G = tri.u_basis(x)
         eps = 0.5 * (G + np.transpose(G, (0, 2, 1)))
         Aeps += wq * np.einsum("aij,bij->ab", eps, eps)
-        g += wq * np.trace(G, axis1=1, axis2=2)
+        dv = np.trace(G, axis1=1, axis2=2)
+        Ddiv += wq * np.outer(dv, dv)
+        g += wq * dv
         psi, divs = tri.w_basis(x)
         Mw += wq * psi @ psi.T
         dw += wq * divs
-    return {"Aeps": Aeps, "g": g, "Mw": Mw, "dw": dw, "area": tri.area}
+    return {"Aeps": Aeps, "Ddiv": Ddiv, "g": g, "Mw": Mw, "dw": dw, "area": tri.area}
 
 
 def element_matrix(parts: dict, prm: Params, kinv: float) -> np.ndarray:
     """13 x 13 element matrix of the reduced-quadrature operator (Sec. 2.3) in local
-    order (ux0..2, uy0..2, b0..2, w0..2, p)."""
+    order (ux0..2, uy0..2, b0..2, w0..2, p).  With ``prm.exact_divdiv`` the grad-div term is
+    lambda (div u, div v) integrated exactly: the original discretisation of Eq. block_form
+    (Sec. 2.1), which Sec. 2.2 and Table 1 show is not solver-friendly."""
     E = np.zeros((13, 13))
     g = parts["g"]
-    E[:9, :9] = 2.0 * prm.mu * parts["Aeps"] + prm.lam * np.outer(g, g) / parts["area"]
+    if getattr(prm, "exact_divdiv", False):
+        E[:9, :9] = 2.0 * prm.mu * parts["Aeps"] + prm.lam * parts["Ddiv"]
+    else:
+        E[:9, :9] = 2.0 * prm.mu * parts["Aeps"] + prm.lam * np.outer(g, g) / parts["area"]
     E[:9, 12] = E[12, :9] = -prm.alpha * g                         # alpha B_u,  B_u = -(div u, q)
     E[9:12, 9:12] = prm.tau * kinv * parts["Mw"]                    # tau M_w
     E[9:12, 12] = E[12, 9:12] = -prm.tau * parts["dw"]              # tau B_w,  B_w = -(div w, q)

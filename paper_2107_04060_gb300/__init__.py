@@ -57,6 +57,8 @@ _sig = {
     "bmg_free_dofs": (C.c_size_t, [C.c_int]),
     "bmg_assemble": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
                                C.c_double, C.c_double, _vp, C.POINTER(_vp)]),
+    "bmg_assemble_divdiv": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_int, _vp, C.POINTER(_vp)]),
     "bmg_assemble_logk": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
                                     C.c_double, _vp, C.POINTER(_vp)]),
     "bmg_adjoint_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -202,15 +204,21 @@ class System:
 
 
 def assemble(n: int, lam: float, mu: float, K=None, K_const: float = 1.0, tau: float = 1.0,
-             alpha: float = 1.0, inv_M: float = 0.0, stream=None) -> System:
-    """``bmg_assemble``: K is None (uniform ``K_const``) or a float64 CUDA tensor laid out
-    as ``pack_k`` produces."""
+             alpha: float = 1.0, inv_M: float = 0.0, stream=None, divdiv: str = "reduced") -> System:
+    """``bmg_assemble`` (``divdiv="reduced"``) or ``bmg_assemble_divdiv`` (``"exact"``: the
+    original discretisation with exactly integrated grad-div term).  K is None (uniform
+    ``K_const``) or a float64 CUDA tensor laid out as ``pack_k`` produces."""
     h = _vp()
     kp = None if K is None else _ptr(K)
-    _check(lib.bmg_assemble(n, lam, mu, kp, K_const, tau, alpha, inv_M, _stream(stream), C.byref(h)),
-           "bmg_assemble")
+    if divdiv == "reduced":
+        _check(lib.bmg_assemble(n, lam, mu, kp, K_const, tau, alpha, inv_M, _stream(stream), C.byref(h)),
+               "bmg_assemble")
+    else:
+        _check(lib.bmg_assemble_divdiv(n, lam, mu, kp, K_const, tau, alpha, inv_M,
+                                       {"reduced": 0, "exact": 1}[divdiv], _stream(stream), C.byref(h)),
+               "bmg_assemble_divdiv")
     return System(h, n, dict(lam=lam, mu=mu, K_const=K_const, tau=tau, alpha=alpha, inv_M=inv_M,
-                             K_field=K is not None))
+                             K_field=K is not None, divdiv=divdiv))
 
 
 def assemble_logk(n: int, lam: float, mu: float, logK, tau: float = 1.0, alpha: float = 1.0,

@@ -130,6 +130,10 @@ extern "C" int bmg_adjoint_gradient(const bmg_system *s, const double *x, const 
     set_error("bmg_adjoint_gradient: NULL argument");
     return BMG_ERR_ARG;
   }
+  if (s->prm.exact_divdiv) {
+    set_error("bmg_adjoint_gradient: the gradients are those of the reduced-quadrature system");
+    return BMG_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const Level &L = s->fine;
   AdjArgs a;

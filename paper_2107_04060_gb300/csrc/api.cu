@@ -189,8 +189,8 @@ extern "C" const char *bmg_last_error(void) { return g_last_error.c_str(); }
 
 // ---- system ----------------------------------------------------------------------------
 static int assemble_impl(int n, double lambda, double mu, const double *K, const float *logK,
-                         double K_const, double tau, double alpha, double inv_M, void *stream,
-                         bmg_system **out) {
+                         double K_const, double tau, double alpha, double inv_M, bool exact_divdiv,
+                         void *stream, bmg_system **out) {
   if (!out) return arg_error("bmg_assemble: out is NULL");
   *out = nullptr;
   if (n < 1 || n > 16384) return arg_error("bmg_assemble: n out of range [1, 16384]");
@@ -214,12 +214,14 @@ static int assemble_impl(int n, double lambda, double mu, const double *K, const
   bmg_system *s = new bmg_system();
   s->n = n;
   s->prm = PhysParams{lambda, mu, tau, alpha, inv_M};
+  s->prm.exact_divdiv = exact_divdiv;
   s->uniform = (K == nullptr && logK == nullptr);
   s->K_const = K_const;
   Level &L = s->fine;
   L.n = n;
   L.g = grid_of(n);
   L.uniform = s->uniform;
+  L.dense_a = exact_divdiv;
   rc = alloc_coefs(L, false);
   if (!rc && cudaMalloc(&s->adj_partial, sizeof(double) * 2 * kAdjBlocks) != cudaSuccess)
     rc = cuda_fail(cudaErrorMemoryAllocation, "bmg_assemble");
@@ -258,13 +260,24 @@ static int assemble_impl(int n, double lambda, double mu, const double *K, const
 extern "C" int bmg_assemble(int n, double lambda, double mu, const double *K, double K_const,
                             double tau, double alpha, double inv_M, void *stream,
                             bmg_system **out) {
-  return assemble_impl(n, lambda, mu, K, nullptr, K_const, tau, alpha, inv_M, stream, out);
+  return assemble_impl(n, lambda, mu, K, nullptr, K_const, tau, alpha, inv_M, false, stream, out);
+}
+
+extern "C" int bmg_assemble_divdiv(int n, double lambda, double mu, const double *K, double K_const,
+                                   double tau, double alpha, double inv_M, int divdiv, void *stream,
+                                   bmg_system **out) {
+  if (divdiv != BMG_DIVDIV_REDUCED && divdiv != BMG_DIVDIV_EXACT) {
+    if (out) *out = nullptr;
+    return arg_error("bmg_assemble_divdiv: divdiv must be BMG_DIVDIV_REDUCED or BMG_DIVDIV_EXACT");
+  }
+  return assemble_impl(n, lambda, mu, K, nullptr, K_const, tau, alpha, inv_M, divdiv == BMG_DIVDIV_EXACT,
+                       stream, out);
 }
 
 extern "C" int bmg_assemble_logk(int n, double lambda, double mu, const float *logK, double tau,
                                  double alpha, double inv_M, void *stream, bmg_system **out) {
   if (!logK) return arg_error("bmg_assemble_logk: logK is NULL");
-  return assemble_impl(n, lambda, mu, nullptr, logK, 0.0, tau, alpha, inv_M, stream, out);
+  return assemble_impl(n, lambda, mu, nullptr, logK, 0.0, tau, alpha, inv_M, false, stream, out);
 }
 
 extern "C" int bmg_system_n(const bmg_system *s) { return s ? s->n : 0; }
@@ -487,12 +500,14 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
       L.c32 = s->fine.c32;
       L.uniform = s->uniform;
       L.wm_full = false;
+      L.dense_a = s->fine.dense_a;
     } else {
       L.uniform = s->uniform;
       L.wm_full = !s->uniform;
       int rc = alloc_coefs(L, L.wm_full);
       if (rc) return fail(rc);
       make_coefs(s->prm, m, &L.c64, &L.c32);
+      L.dense_a = s->prm.exact_divdiv;
       if (o->coarse_op == BMG_GALERKIN) {
         galerkin_coarsen_coefs(h->levels[h->levels.size() - 2].c64, &L.c64, &L.c32);
         L.dense_a = true;

@@ -740,6 +740,8 @@ extern "C" int bmg_batch_create(bmg_hierarchy *const *hs, int count, const bmg_k
       return batch_error("bmg_batch_create: hierarchies must use V-cycles (gamma 0 or 1)");
     if (mo.coarse_op != BMG_REDISC)
       return batch_error("bmg_batch_create: hierarchies must use rediscretised coarse operators");
+    if (h->sys->prm.exact_divdiv)
+      return batch_error("bmg_batch_create: systems must use the reduced-quadrature grad-div term");
     const bmg_mg_opts &o0 = hs[0]->opts;
     if (mo.nu1 < 1 || mo.nu1 != o0.nu1 || mo.nu2 != o0.nu2 || mo.n_coarse != o0.n_coarse)
       return batch_error("bmg_batch_create: hierarchies must share nu1 >= 1, nu2 and n_coarse");

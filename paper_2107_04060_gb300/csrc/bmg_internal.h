@@ -40,6 +40,7 @@ inline Grid grid_of(int n) { return Grid{n, pitch_of(n), block_len_of(n)}; }
 // h(i,j)); U(i,j) = {(i+1,j+1), (i,j+1), (i+1,j)}, edges (d(i,j), v(i+1,j), h(i,j+1)).
 struct ElemIntegrals {
   double Aeps[2][9][9];   // int eps(phi_a) : eps(phi_b)
+  double Ddiv[2][9][9];   // int div phi_a div phi_b (exact; the divergence of a bubble is linear)
   double g[2][9];         // int div phi_a
   double Mw[2][3][3];     // int psi_a . psi_b
   double dw[2][3];        // int div psi_a
@@ -76,6 +77,9 @@ bool verify_elem_nonzeros(std::string *why);
 
 struct PhysParams {
   double lambda, mu, tau, alpha, inv_M;
+  bool exact_divdiv = false;   // lambda (div u, div v) integrated exactly (Sec. 2.1) instead of
+                               // the reduced quadrature (Sec. 2.3): dense displacement element
+                               // matrices 2 mu A_eps + lambda D, lam_area = 0
 };
 
 void make_coefs(const PhysParams &p, int n, OpCoefs<double> *c64, OpCoefs<float> *c32);

@@ -139,6 +139,7 @@ void element_integrals(double h, ElemIntegrals *out) {
           for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 2; ++c) s += eps[a][r][c] * eps[b][r][c];
           out->Aeps[o][a][b] += wq * s;
+          out->Ddiv[o][a][b] += wq * div[a] * div[b];
         }
       }
       double psi[3][2], dv[3];
@@ -191,14 +192,15 @@ void make_coefs(const PhysParams &p, int n, OpCoefs<double> *c64, OpCoefs<float>
   for (int o = 0; o < 2; ++o) {
     for (int a = 0; a < 9; ++a) {
       c.g[o][a] = e.g[o][a];
-      for (int b = 0; b < 9; ++b) c.A[o][a * 9 + b] = 2.0 * p.mu * e.Aeps[o][a][b];
+      for (int b = 0; b < 9; ++b)
+        c.A[o][a * 9 + b] = 2.0 * p.mu * e.Aeps[o][a][b] + (p.exact_divdiv ? p.lambda * e.Ddiv[o][a][b] : 0.0);
     }
     for (int a = 0; a < 3; ++a) {
       c.dw[o][a] = p.tau * e.dw[o][a];
       for (int b = 0; b < 3; ++b) c.M1[o][a * 3 + b] = p.tau * e.Mw[o][a][b];
     }
   }
-  c.lam_area = p.lambda / e.area;
+  c.lam_area = p.exact_divdiv ? 0.0 : p.lambda / e.area;
   c.alpha = p.alpha;
   c.pp = p.inv_M * e.area;
   if (c32) {

@@ -285,3 +285,51 @@ def test_galerkin_converges_where_rediscretisation_stagnates(bmg):
     _, oinfo = krylov.fgmres(H.levels[0].A, H.levels[0].mesh.pack(f), H.vcycle, rtol=1e-8,
                              restart=50, maxit=400)
     assert oinfo["converged"] and abs(ig["iters"] - oinfo["iters"]) <= 1, (ig["iters"], oinfo["iters"])
+
+
+@pytest.mark.parametrize("n", [8, 33])
+def test_exact_divdiv_apply_parity(bmg, n):
+    """bmg_assemble_divdiv(BMG_DIVDIV_EXACT): the original discretisation (Sec. 2.1, exact
+    (div u, div v)) against the oracle's assembly with exact_divdiv, lognormal K, 1e-12."""
+    import torch
+    p = dict(lam=1e4, mu=1.3, tau=0.5, alpha=0.8, inv_M=1e-2)
+    kL, kU = synthetic.lognormal_k(n, 1.5, 40 + n)
+    s = bmg.assemble(n, p["lam"], p["mu"], kfield(bmg, n, kL, kU), 0.0, p["tau"], p["alpha"], p["inv_M"],
+                     divdiv="exact")
+    f = synthetic.uniform_field(n, 50 + n)
+    x = dev(bmg, n, f)
+    y = torch.empty_like(x)
+    s.apply(x, y)
+    m = Mesh(n)
+    A = fem.assemble(m, fem.Params(exact_divdiv=True, **p), 1 / kL, 1 / kU)
+    assert relmax(to_oracle(bmg, m, y), A @ m.pack(f)) < 1e-12
+
+
+@pytest.mark.parametrize("smoother,omega", [("vanka", 0.7), ("bsr", 0.6)])
+def test_exact_divdiv_vcycle_parity_and_degradation(bmg, smoother, omega):
+    """V-cycle of the exact-div-div system against the oracle's (n = 32), and FGMRES counts
+    at lambda / mu = 499 (nu = 0.499), K = 1e-6, n = 64: the exact form needs several times
+    the reduced-quadrature form's iterations (the negative control of Table 1)."""
+    import torch
+    n = 32
+    p = dict(lam=499.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1e-2)
+    s = bmg.assemble(n, p["lam"], p["mu"], None, 1e-6, p["tau"], p["alpha"], p["inv_M"], divdiv="exact")
+    h = bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8)
+    kinv = np.full((n, n), 1e6)
+    H = mg.Hierarchy(n, fem.Params(exact_divdiv=True, **p), kinv, kinv, smoother=smoother, omega=omega,
+                     omega_J=1.0, nu1=1, nu2=1, n_coarse=8)
+    f = synthetic.rhs(n, 10)
+    r = dev(bmg, n, f)
+    z = torch.empty_like(r)
+    h.vcycle(r, z)
+    zo = H.vcycle(H.levels[0].mesh.pack(f))
+    assert relmax(to_oracle(bmg, H.levels[0].mesh, z), zo) < 1e-9
+    n = 64
+    its = {}
+    for dd in ("reduced", "exact"):
+        s = bmg.assemble(n, p["lam"], p["mu"], None, 1e-6, p["tau"], p["alpha"], p["inv_M"], divdiv=dd)
+        h = bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8)
+        b = dev(bmg, n, synthetic.rhs(n, 0))
+        x = torch.zeros_like(b)
+        its[dd] = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=1500)["iters"]
+    assert its["exact"] >= 2 * its["reduced"], its

@@ -203,3 +203,20 @@ def test_apply_rows_matches_assembled_operator(prm):
     scale = np.max(np.abs(want))
     assert np.max(np.abs(got - want)) <= 1e-13 * scale
     assert np.all(got[m.fixed] == 0.0)
+
+
+def test_exact_divdiv_element_dominates_reduced_quadrature():
+    """The exactly integrated grad-div element matrix D = (div phi_a, div phi_b) (Sec. 2.1)
+    and its reduced-quadrature form g g^T / |T| (Sec. 2.3): the divergence of P1 + bubble is
+    linear on a triangle, so D has rank 3, D - g g^T / |T| is positive semidefinite (Cauchy-
+    Schwarz), and the two agree on P1 fields (constant divergence)."""
+    for tri in fem.reference_triangles(8).values():
+        parts = fem.element_parts(tri)
+        D, g, area = parts["Ddiv"], parts["g"], parts["area"]
+        assert np.linalg.matrix_rank(D, tol=1e-12 * np.abs(D).max()) == 3
+        ev = np.linalg.eigvalsh(D - np.outer(g, g) / area)
+        assert ev.min() > -1e-12 * np.abs(D).max()
+        P1 = np.zeros((9, 6))
+        P1[:6, :6] = np.eye(6)
+        diff = P1.T @ (D - np.outer(g, g) / area) @ P1
+        assert np.abs(diff).max() <= 1e-12 * np.abs(D).max()

@@ -83,3 +83,18 @@ def test_galerkin_coarse_grid_correction_is_a_projection_and_rescues_small_inv_m
     assert rho_cgc(tr) > 2.0
     assert tr.rho(0.8, 1, 1) > 1.0
     assert tg.rho(0.8, 1, 1) < 0.85
+
+
+def test_table1_exact_divdiv_degrades_while_reduced_quadrature_stays_robust():
+    """Table 1 / Sec. 2.2 negative control: with lambda (div u, div v) integrated exactly (the
+    original discretisation) the two-grid factor of additive Vanka V(2,2) at nu = 0.499,
+    k = 1e-6, h = 1/64 is 0.970 (the measured factor printed in Table 1), inexact BSR V(1,1) is
+    above 0.95 (Table 1: 0.968); with reduced quadrature the same Vanka cycle gives about 0.6
+    (Table 2's regime); at nu = 0.4 the two discretisations give the same factor."""
+    def tg(nu, exact, smoother):
+        prm = fem.Params.from_paper(3e4, nu, tau=1.0, alpha=1.0, inv_M=1e-6, exact_divdiv=exact)
+        return lfa.TwoGrid(prm, 1e-6, 1 / 64, smoother, samples=16)
+    assert tg(0.499, True, "vanka").rho(0.70, 2, 2) == pytest.approx(0.970, abs=3e-3)
+    assert tg(0.499, False, "vanka").rho(0.70, 2, 2) < 0.62
+    assert tg(0.499, True, "bsr").rho(0.60, 1, 1, 1.0) > 0.95
+    assert tg(0.4, True, "vanka").rho(0.78, 2, 2) == pytest.approx(tg(0.4, False, "vanka").rho(0.78, 2, 2), abs=1e-3)
