@@ -317,17 +317,23 @@ def run_micro(args):
     torch.cuda.synchronize()
     bmg.profile_start(fam, n)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")           # ncu --nvtx-include timed/ selects these launches
     ev0.record()
     for _ in range(args.reps):
         run()
     ev1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     prof = bmg.profile_stop()
     avg = prof["ms"] / max(prof["launches"], 1)
     cells = prof["cells"] / max(prof["launches"], 1)
     bpc = BYTES_PER_CELL_F64[fam] * (0.5 if args.precision == "fp32" else 1.0)
+    tiles = None
+    if h is not None:
+        tiles = {str(n >> l): [h.tile(l, "apply"), h.tile(l, "vanka"), h.tile(l, "vanka_u")]
+                 for l in range(h.levels - 1)}
     print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision, "uniform_k": args.uniform_k,
-                      "residual": args.residual,
+                      "residual": args.residual, "tiles_apply_vanka_vankau": tiles,
                       "gbs_algorithmic_this_precision": bpc * cells / (avg * 1e-3) / 1e9,
                       "call_ms": ev0.elapsed_time(ev1) / args.reps, "kernel": fam,
                       "kernel_avg_ms": avg, "launches": prof["launches"],
