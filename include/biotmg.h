@@ -254,8 +254,20 @@ int bmg_adjoint_gradient(const bmg_system *s, const double *x, const double *xi,
 #define BMG_PROF_COARSE 6     /* coarsest-grid solve                                   */
 #define BMG_PROF_KRYLOV 7     /* FGMRES vector kernels (dots, updates, scaling)         */
 int bmg_profile_start(int kernel, int n);
-/* Number of kernels this library has launched in the process so far (host-side count). */
+/* Number of kernels this library has launched in the process so far (host-side count; a
+ * replayed V-cycle graph counts its kernel nodes). */
 long long bmg_launch_count(void);
+
+/*
+ * bmg_use_graphs -- V-cycles as CUDA graphs, process-wide (default on; the environment
+ * variable BMG_NO_GRAPHS=1 starts with it off).  When on, the second and later V-cycles of a
+ * hierarchy on a non-default stream are captured once per (input, output) vector pair and
+ * replayed with one graph launch instead of a launch per kernel (the levels below about 128^2
+ * cost more to launch than to run).  Results are identical either way.  Kernel timing
+ * (bmg_profile_start) brackets only launches made kernel by kernel, so a caller that wants
+ * the V-cycle's kernels timed turns graphs off.  Returns the previous setting.
+ */
+int bmg_use_graphs(int enable);
 int bmg_profile_stop(double *total_ms, long long *launches, double *cells);
 
 /*

@@ -78,6 +78,7 @@ _sig = {
     "bmg_status_string": (C.c_char_p, [C.c_int]),
     "bmg_profile_start": (C.c_int, [C.c_int, C.c_int]),
     "bmg_launch_count": (C.c_longlong, []),
+    "bmg_use_graphs": (C.c_int, [C.c_int]),
     "bmg_profile_stop": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "bmg_last_error": (C.c_char_p, []),
     "bmg_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(KrylovOpts), C.c_int, _vp,
@@ -376,6 +377,12 @@ def noalloc_capacity() -> int:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return lib.bmg_launch_count()
+
+
+def use_graphs(enable: bool) -> bool:
+    """``bmg_use_graphs``: V-cycles replayed as CUDA graphs (True by default); returns the
+    previous setting."""
+    return bool(lib.bmg_use_graphs(1 if enable else 0))
 
 
 def profile_start(kernel: str, n: int = 0):

@@ -106,6 +106,17 @@ struct ProfState {
 static ProfState g_prof;
 static std::mutex g_prof_mutex;
 
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// V-cycles replayed from CUDA graphs (bmg_use_graphs); on unless BMG_NO_GRAPHS is set
+static std::atomic<int> g_use_graphs{[] {
+  const char *e = std::getenv("BMG_NO_GRAPHS");
+  return (e && *e && *e != '0') ? 0 : 1;
+}()};
+
 bool prof_on(int kernel, int n) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   return g_prof.kernel != 0 && g_prof.kernel == kernel && (g_prof.n == 0 || g_prof.n == n);
@@ -131,6 +142,8 @@ void prof_end(cudaStream_t st, cudaEvent_t e0, double cells) {
 using namespace bmg;
 
 extern "C" long long bmg_launch_count(void) { return g_launches.load(); }
+
+extern "C" int bmg_use_graphs(int enable) { return g_use_graphs.exchange(enable ? 1 : 0); }
 
 extern "C" int bmg_profile_start(int kernel, int n) {
   if (kernel < 1 || kernel > 7 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");
@@ -595,8 +608,11 @@ extern "C" int bmg_hierarchy_tile(const bmg_hierarchy *h, int level, int kernel)
   }
 }
 
+static void drop_graphs(bmg_hierarchy *h);
+
 extern "C" void bmg_destroy_hierarchy(bmg_hierarchy *h) {
   if (!h) return;
+  drop_graphs(h);
   for (auto &L : h->levels) free_level(L);
   cudaFree(h->d_flag);
   cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->r); cudaFree(h->xb);
@@ -657,7 +673,7 @@ static int vcycle_level(bmg_hierarchy *h, size_t l, const T *rhs, T *z, cudaStre
   return BMG_OK;
 }
 
-static int vcycle_any(bmg_hierarchy *h, const double *r, double *z, cudaStream_t st) {
+static int vcycle_direct(bmg_hierarchy *h, const double *r, double *z, cudaStream_t st) {
   if (h->opts.precision == BMG_FP64) return vcycle_level<double>(h, 0, r, z, st);
   Level &L = h->levels[0];
   const size_t vl = vec_len_of(L.n);
@@ -665,6 +681,66 @@ static int vcycle_any(bmg_hierarchy *h, const double *r, double *z, cudaStream_t
   if (rc) return rc;
   if ((rc = vcycle_level<float>(h, 0, (const float *)L.rhs, (float *)L.t2, st))) return rc;
   return launch_convert_f2d((const float *)L.t2, z, vl, st);
+}
+
+static void drop_graphs(bmg_hierarchy *h) {
+  for (auto &g : h->vgraphs) cudaGraphExecDestroy(g.exec);
+  h->vgraphs.clear();
+}
+
+// One V-cycle.  A cycle is a fixed sequence of some tens of small launches, most of them on the
+// coarse levels where each costs more to launch than to run, so after a first cycle launched
+// kernel by kernel (which also runs every one-time initialisation of the kernels it uses) the
+// sequence is captured once per (r, z) pair as a CUDA graph and replayed with one launch.
+// Graphs are not used on the legacy default stream (it cannot be captured), inside a capture
+// of the caller's (the launches then join that capture), or while bmg_use_graphs(0) is in
+// effect.  Kernel timing (bmg_profile_start) sees only launches made kernel by kernel.
+constexpr size_t kMaxVcGraphs = 160;
+
+static int vcycle_any(bmg_hierarchy *h, const double *r, double *z, cudaStream_t st) {
+  if (!g_use_graphs.load() || st == nullptr || h->vcycles_direct == 0 || h->graphs_failed ||
+      capturing(st)) {
+    ++h->vcycles_direct;
+    return vcycle_direct(h, r, z, st);
+  }
+  for (const auto &g : h->vgraphs)
+    if (g.r == r && g.z == z) {
+      BMG_CUDA(cudaGraphLaunch(g.exec, st));
+      g_launches += g.kernels;
+      return BMG_OK;
+    }
+  if (h->vgraphs.size() >= kMaxVcGraphs) drop_graphs(h);
+  const long long before = g_launches.load();
+  BMG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = vcycle_direct(h, r, z, st);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  g_launches = before;                      // the captured launches have not run
+  if (rc || e != cudaSuccess) {              // launch kernel by kernel from now on
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    h->graphs_failed = true;
+    ++h->vcycles_direct;
+    return vcycle_direct(h, r, z, st);
+  }
+  VcGraph g;
+  g.r = r;
+  g.z = z;
+  size_t nodes = 0;
+  e = cudaGraphGetNodes(graph, nullptr, &nodes);
+  if (e == cudaSuccess) e = cudaGraphInstantiateWithFlags(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    h->graphs_failed = true;
+    ++h->vcycles_direct;
+    return vcycle_direct(h, r, z, st);
+  }
+  g.kernels = (long long)nodes;
+  h->vgraphs.push_back(g);
+  BMG_CUDA(cudaGraphLaunch(g.exec, st));
+  g_launches += g.kernels;
+  return BMG_OK;
 }
 
 extern "C" int bmg_vcycle(bmg_hierarchy *h, const double *r, double *z, void *stream) {

@@ -255,10 +255,22 @@ struct bmg_system {
   double *adj_partial = nullptr;   // [2][kAdjBlocks] partial sums of the Lame gradients
 };
 
+namespace bmg {
+// One V-cycle captured as a CUDA graph for a given (input, output) pair of device vectors.
+struct VcGraph {
+  const void *r = nullptr, *z = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;       // kernel nodes (added to the launch count per replay)
+};
+}  // namespace bmg
+
 struct bmg_hierarchy {
   const bmg_system *sys;
   bmg_mg_opts opts;
   std::vector<bmg::Level> levels;
+  std::vector<bmg::VcGraph> vgraphs;   // captured V-cycles (see vcycle_any)
+  long long vcycles_direct = 0;        // cycles launched kernel by kernel
+  bool graphs_failed = false;          // a capture failed: launch kernel by kernel from now on
   int *d_flag = nullptr;       // device error flag (singular pivots)
   bmg::Level fine_op;          // the system's fine level with the FP64 operator tile tuned
                                // for this device (FGMRES matvec and true residual)
@@ -299,12 +311,14 @@ extern std::atomic<long long> g_launches;
 // ---- kernel timing (bmg_profile_start / bmg_profile_stop) ------------------------------
 namespace bmg {
 bool prof_on(int kernel, int n);
+bool capturing(cudaStream_t st);     // st is being captured into a graph
 cudaEvent_t prof_begin(cudaStream_t st);
 void prof_end(cudaStream_t st, cudaEvent_t e0, double cells);
 }  // namespace bmg
 
 #define BMG_PROF_BEGIN(kid, n, st) \
-  const bool prof_ = bmg::prof_on(kid, n); cudaEvent_t prof_e0_ = prof_ ? bmg::prof_begin(st) : nullptr
+  const bool prof_ = bmg::prof_on(kid, n) && !bmg::capturing(st); \
+  cudaEvent_t prof_e0_ = prof_ ? bmg::prof_begin(st) : nullptr
 #define BMG_PROF_END(st, cells) if (prof_) bmg::prof_end(st, prof_e0_, cells)
 
 // ---- kernel launchers (implemented in the .cu files) -----------------------------------
