@@ -732,16 +732,21 @@ def main():
         hs_ = hier if hset is None else hset
         todo = [ci for ci in range(len(cases)) if subset is None or ci in subset]
         if nstreams == 1 and solve is None:
+            cur = torch.cuda.current_stream()
+            streams[0].wait_stream(cur)
             for ci in todo:
                 c = cases[ci]
-                flush.fill_(float(ci))
-                info = hs_[prec, ci].fgmres_solve(rhs[c["seed"]], x, rtol=RTOL, restart=RESTART,
-                                                  maxit=maxit, x0_is_zero=True, arnoldi=arnoldi)
+                with torch.cuda.stream(streams[0]):
+                    flush.fill_(float(ci))
+                    info = hs_[prec, ci].fgmres_solve(rhs[c["seed"]], x, rtol=RTOL, restart=RESTART,
+                                                      maxit=maxit, x0_is_zero=True, arnoldi=arnoldi,
+                                                      stream=streams[0])
                 if info["status"] != "converged" and not allow_fail:
                     raise RuntimeError(f"solve did not converge: {c} {info}")
                 cost[ci] = info["iters"]
                 if record is not None:
                     record.append((c, info))
+            cur.wait_stream(streams[0])
             return
         # independent solves on nstreams streams, one host thread each (the library calls
         # release the interpreter lock); L2 flushed once before the step
