@@ -880,6 +880,28 @@ def main():
     if "fp32" in precisions:
         ms32, recs32, _, _ = timed("fp32", args.steps, subset=fp32_cases)
         ms64s, _, _, _ = timed("fp64", args.steps, subset=fp32_cases)
+    # lambda / mu = 1e6 with FP32 V-cycles: FP32 patch solves, FP64 patch solves, and the FP64
+    # V-cycle, Vanka, both K (the FP32 arm above stops at lambda = 1e4)
+    probe64 = None
+    if "fp32" in precisions and not args.no_arms:
+        probe64 = []
+        for ci in [ci for ci, c in enumerate(cases) if c["lam"] == 1e6 and c["smoother"] == "vanka"]:
+            c = cases[ci]
+            row = {"lam": c["lam"], "K": c["K"]}
+            for label, kw in (("fp32", dict(precision="fp32")),
+                              ("fp32_patch_fp64", dict(precision="fp32", patch_solve="fp64")),
+                              ("fp64", dict(precision="fp64"))):
+                hp = bmg.setup_hierarchy(systems[c["lam"], c["K"]], "vanka", 1, 1, omega=c["omega"],
+                                         n_coarse=8, **kw)
+                xp = torch.zeros_like(rhs[c["seed"]])
+                t0 = time.perf_counter()
+                ip = hp.fgmres_solve(rhs[c["seed"]], xp, rtol=RTOL, restart=RESTART, maxit=MAXIT_ARM,
+                                     stream=streams[0])
+                row[label] = {"iters": ip["iters"], "status": ip["status"],
+                              "relres": float(f"{ip['relres']:.3g}"),
+                              "s": round(time.perf_counter() - t0, 3)}
+                del hp
+            probe64.append(row)
     # the same 12 FP64 solves with the mixed-precision Arnoldi (FP32 first Gram-Schmidt pass,
     # double-float second pass and correction)
     arm_steps = max(1, min(args.steps, 5))
@@ -971,6 +993,7 @@ def main():
                           "fp64_same_solves": {"value": sub_dofs / (ms64s * 1e-3) / 1e6, "ms_per_step": ms64s},
                           "speedup_vs_fp64": ms64s / ms32,
                           "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]],
+                          "lambda_1e6_probe": probe64,
                           "vcycle_hbm": {"unit": "GB/s algorithmic, fine level, FP32 V-cycles of the 8 "
                                                  "hierarchies (3 each) alone on the GPU",
                                          "peak_gbs": measured_hbm_gbs()[0],

@@ -74,6 +74,8 @@ extern "C" {
 #define BMG_BSR 1             /* inexact Braess-Sarazin (Sec. 3.2.2, App. D)            */
 #define BMG_FP64 0
 #define BMG_FP32 1
+#define BMG_PATCH_CYCLE 0     /* Vanka patch solves in the V-cycle's precision             */
+#define BMG_PATCH_FP64 1      /* FP32 V-cycle with FP64 patch solves (FP64 inverses)       */
 #define BMG_REDISC 0          /* coarse operators by rediscretisation (Sec. 3, the paper's) */
 #define BMG_GALERKIN 1        /* coarse operators P^T A P (R = P^T, Eq. block_interp)      */
 
@@ -158,6 +160,9 @@ typedef struct {
                        grad-div block is exactly 4 x its rediscretisation per level (the whole
                        divergence of a coarse triangle lands in its interior child), and the
                        RT0 and P0 blocks equal their rediscretisation (nested spaces)        */
+  int patch_solve;  /* BMG_PATCH_CYCLE (0) or BMG_PATCH_FP64: with precision BMG_FP32 and the
+                       Vanka smoother, the patch solves use the FP64 inverses and FP64 products
+                       (vectors, residuals and transfers stay FP32); ignored otherwise        */
 } bmg_mg_opts;
 
 /*

@@ -33,7 +33,8 @@ STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "diverged"}
 class MgOpts(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("omega", C.c_double),
                 ("omega_J", C.c_double), ("n_coarse", C.c_int), ("precision", C.c_int),
-                ("p_shift", C.c_double), ("gamma", C.c_int), ("coarse_op", C.c_int)]
+                ("p_shift", C.c_double), ("gamma", C.c_int), ("coarse_op", C.c_int),
+                ("patch_solve", C.c_int)]
 
 
 class KrylovOpts(C.Structure):
@@ -304,12 +305,13 @@ def _info(info: SolveInfo) -> dict:
 def setup_hierarchy(system: System, smoother: str = "vanka", nu1: int = 1, nu2: int = 1,
                     omega: float = 0.8, omega_J: float = 1.0, n_coarse: int = 8,
                     precision: str = "fp64", p_shift: float = 0.0, cycle: str = "V",
-                    coarse_op: str = "redisc", stream=None) -> Hierarchy:
+                    coarse_op: str = "redisc", patch_solve: str = "cycle", stream=None) -> Hierarchy:
     """``bmg_setup_hierarchy``; ``cycle`` is "V" or "W" (gamma = 1 or 2), ``coarse_op``
-    "redisc" (the paper's) or "galerkin"."""
+    "redisc" (the paper's) or "galerkin", ``patch_solve`` "cycle" or "fp64" (FP64 Vanka
+    patch solves inside an FP32 V-cycle)."""
     o = MgOpts(VANKA if smoother == "vanka" else BSR, nu1, nu2, omega, omega_J, n_coarse,
                FP64 if precision == "fp64" else FP32, p_shift, {"V": 1, "W": 2}[cycle],
-               {"redisc": 0, "galerkin": 1}[coarse_op])
+               {"redisc": 0, "galerkin": 1}[coarse_op], {"cycle": 0, "fp64": 1}[patch_solve])
     h = _vp()
     _check(lib.bmg_setup_hierarchy(system.handle, C.byref(o), _stream(stream), C.byref(h)),
            "bmg_setup_hierarchy")

@@ -483,6 +483,8 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
     return arg_error("bmg_setup_hierarchy: gamma must be 0 or 1 (V-cycle) or 2 (W-cycle)");
   if (o->coarse_op != BMG_REDISC && o->coarse_op != BMG_GALERKIN)
     return arg_error("bmg_setup_hierarchy: coarse_op must be BMG_REDISC or BMG_GALERKIN");
+  if (o->patch_solve != BMG_PATCH_CYCLE && o->patch_solve != BMG_PATCH_FP64)
+    return arg_error("bmg_setup_hierarchy: patch_solve must be BMG_PATCH_CYCLE or BMG_PATCH_FP64");
   const int n = s->n;
   if (o->n_coarse < 2 || o->n_coarse > 64 || n < o->n_coarse || n % o->n_coarse)
     return arg_error("bmg_setup_hierarchy: need 2 <= n_coarse <= 64 dividing n");
@@ -548,6 +550,7 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
       cudaMemsetAsync(L.wz, 0, es * vl, st);
     }
     L.err = h->d_flag;
+    L.solve64 = fp32 && o->smoother == BMG_VANKA && o->patch_solve == BMG_PATCH_FP64;
     // FP32 operator input staged by TMA: the V-cycle applies the operator to z (to t2 on the
     // finest level); tuning decides whether that variant runs
     if (fp32 && m != o->n_coarse) {

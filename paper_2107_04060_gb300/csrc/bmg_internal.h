@@ -124,6 +124,7 @@ struct Level {
   bool wm_full = false;        // per-triangle 3x3 RT0 mass (coarse levels, varying K)
   bool uniform = false;        // every triangle has the same coefficients
   bool dense_a = false;        // Galerkin coarse level: dense elasticity element matrices
+  bool solve64 = false;        // FP32 V-cycle: Vanka patch solves in FP64 (BMG_PATCH_FP64)
   double *kinv64 = nullptr;    // [2][blk] per-triangle K^{-1} (wm_full == false)
   float *kinv32 = nullptr;
   double *wm64 = nullptr;      // [2][6][blk] symmetric 3x3 RT0 mass incl. tau (wm_full)

@@ -339,25 +339,27 @@ int launch_vanka_setup(const Level &L, const int *rep_i, const int *rep_j, int n
 // issues 20 * (rows per thread) FP64 FMAs instead of 400 (the FP64 pipe of a GB300 SM
 // retires about two FMAs per clock, so the per-warp instruction count sets the time);
 // phase 3 gathers the weighted corrections.  Deterministic, no atomics.
-template <typename T>
+// T: vectors and weighted gather; S: the patch solves (the inverses and their products).
+// S = double with T = float is the FP32 sweep with FP64 patch solves (BMG_PATCH_FP64).
+template <typename T, typename S = T>
 struct VankaSweepArgs {
   Grid g;
   const T *r;
   T *x;
   const int *slot;
-  const T *inv;
+  const S *inv;
   int nslots;
   T omega;
   int assign;   // 1: x <- omega M^{-1} r on the free DoFs (x was zero); 0: x += omega M^{-1} r
   const int *gate;
   int klein;    // slot 0 also given in the symmetry-adapted basis (kb)
-  T kb[20][7];
+  S kb[20][7];
 };
 
 // kKlein = false compiles the symmetry-adapted path out (slot-0 patches then use the dense
 // inverse, which is always stored): fewer registers where that path is not used.
-template <typename T, int kPX, int kPY, int NT, bool kKlein = true>
-__device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, int by) {
+template <typename T, int kPX, int kPY, int NT, bool kKlein = true, typename S = T>
+__device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T, S> &a, int bx, int by) {
   constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
   // dynamic shared memory (vanka_smem_bytes): residuals sr[NP][LD], corrections sx[NP][LD],
   // inverse slots ss[NP]
@@ -416,11 +418,13 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       for (int c = 0; c < 20; ++c) sr[p * LD + c] = r[c];
       if (sl != 0) s_mixed = 1;
     } else if (kl && sl == 0) {
-      T q[20], xq[20], x[20];
-      klein_fwd(r, q);
+      S rs[20], q[20], xq[20], x[20];
+#pragma unroll
+      for (int c = 0; c < 20; ++c) rs[c] = (S)r[c];
+      klein_fwd(rs, q);
       static_for<20>([&](auto k_) {
         constexpr int k = decltype(k_)::value, b0 = klein_block_start(k);
-        T acc = 0;
+        S acc = 0;
         static_for<klein_block_size(k)>([&](auto l_) {
           constexpr int l = decltype(l_)::value;
           acc = fma(a.kb[k][l], q[b0 + l], acc);
@@ -429,7 +433,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       });
       klein_inv(xq, x);
 #pragma unroll
-      for (int c = 0; c < 20; ++c) sx[p * LD + c] = x[c];
+      for (int c = 0; c < 20; ++c) sx[p * LD + c] = (T)x[c];
     } else {
 #pragma unroll
       for (int c = 0; c < 20; ++c) sr[p * LD + c] = r[c];
@@ -445,16 +449,16 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       for (int t = tid; t < NP * 20; t += NT) {
         const int row = t / NP, p = t % NP;
         if (ss[p] == 0) continue;
-        const T *inv = a.inv + ss[p];
+        const S *inv = a.inv + ss[p];
         const int rb = sym20_row_base(row);
         const T *rl = sr + p * LD;
-        T acc = 0;
+        S acc = 0;
 #pragma unroll
         for (int c = 0; c < 20; ++c) {
           const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
-          acc = fma(inv[(size_t)e * ld], rl[c], acc);
+          acc = fma(inv[(size_t)e * ld], (S)rl[c], acc);
         }
-        sx[p * LD + row] = acc;
+        sx[p * LD + row] = (T)acc;
       }
     }
   } else if (!s_mixed) {
@@ -465,7 +469,7 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
     constexpr int NG = NT / 20;
     if (tid < NG * 20) {
       const int row = tid % 20, grp = tid / 20;
-      T irow[20];
+      S irow[20];
       const int rb = sym20_row_base(row);
 #pragma unroll
       for (int c = 0; c < 20; ++c) {
@@ -474,10 +478,10 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
       }
       for (int p = grp; p < NP; p += NG) {
         const T *rl = sr + p * LD;
-        T acc = 0;
+        S acc = 0;
 #pragma unroll
-        for (int c = 0; c < 20; ++c) acc = fma(irow[c], rl[c], acc);
-        sx[p * LD + row] = acc;
+        for (int c = 0; c < 20; ++c) acc = fma(irow[c], (S)rl[c], acc);
+        sx[p * LD + row] = (T)acc;
       }
     }
   } else {
@@ -485,20 +489,20 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
     // take consecutive patches of one row, so their inverse loads coalesce (or broadcast);
     // in FP32 four tasks per step keep 80 independent factor loads in flight per thread (the
     // FP64 sweep is bound by the FP64 pipe instead and keeps its registers)
-    constexpr int kUnroll = sizeof(T) == 4 ? 4 : 1;
+    constexpr int kUnroll = sizeof(S) == 4 ? 4 : 1;
 #pragma unroll kUnroll
     for (int t = tid; t < NP * 20; t += NT) {
       const int row = t / NP, p = t % NP;
-      const T *inv = a.inv + ss[p];
+      const S *inv = a.inv + ss[p];
       const int rb = sym20_row_base(row);
       const T *rl = sr + p * LD;
-      T acc = 0;
+      S acc = 0;
 #pragma unroll
       for (int c = 0; c < 20; ++c) {
         const int e = c < row ? c * 19 - (c * (c - 1)) / 2 + row : rb + c;
-        acc = fma(inv[(size_t)e * ld], rl[c], acc);
+        acc = fma(inv[(size_t)e * ld], (S)rl[c], acc);
       }
-      sx[p * LD + row] = acc;
+      sx[p * LD + row] = (T)acc;
     }
   }
   __syncthreads();
@@ -541,11 +545,11 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T> &a, int bx, i
   }
 }
 
-template <typename T, int kPX, int kPY, int NT>
-__global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T> a) {
+template <typename T, int kPX, int kPY, int NT, typename S>
+__global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T, S> a) {
   pdl_enter();
   BMG_GATE(a.gate);
-  vanka_tile<T, kPX, kPY, NT>(a, blockIdx.x, blockIdx.y);
+  vanka_tile<T, kPX, kPY, NT, true, S>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batched form: blockIdx.z selects one of several instances of one grid size; their
@@ -562,41 +566,40 @@ constexpr size_t vanka_smem_bytes() {
   return 2 * (size_t)PX * PY * 21 * sizeof(T) + (size_t)PX * PY * sizeof(int);
 }
 
-template <typename T, int PX, int PY, int NT>
-static void launch_vanka_tile(const VankaSweepArgs<T> &a, const Level &L, cudaStream_t st) {
+template <typename T, int PX, int PY, int NT, typename S>
+static void launch_vanka_tile(const VankaSweepArgs<T, S> &a, const Level &L, cudaStream_t st) {
   constexpr size_t smem = vanka_smem_bytes<T, PX, PY>();
   static_assert(smem <= 200 * 1024, "shared memory of a Vanka tile");
   if constexpr (smem > 48 * 1024) {
     static const bool opted_in = [] {          // once per instantiation, thread-safe
-      return cudaFuncSetAttribute(vanka_sweep_kernel<T, PX, PY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      return cudaFuncSetAttribute(vanka_sweep_kernel<T, PX, PY, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem) == cudaSuccess;
     }();
     (void)opted_in;
   }
   dim3 grid((L.g.pitch + PX - 2) / (PX - 1), (L.n + 1 + PY - 2) / (PY - 1));
-  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT>, dim3(grid), dim3(NT), smem, st, a);
+  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT, S>, dim3(grid), dim3(NT), smem, st, a);
 }
 
 static long long vanka_ctas(const Level &L, int px, int py) {
   return (long long)((L.g.pitch + px - 2) / (px - 1)) * ((L.n + 1 + py - 2) / (py - 1));
 }
 
-template <typename T>
-int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
-  VankaSweepArgs<T> a;
+template <typename T, typename S>
+static void launch_vanka_sweep_s(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
+  VankaSweepArgs<T, S> a;
   a.g = L.g;
   a.r = r;
   a.x = x;
   a.slot = L.slot;
-  a.inv = (const T *)(sizeof(T) == 8 ? (const void *)L.pinv64 : (const void *)L.pinv32);
+  a.inv = (const S *)(sizeof(S) == 8 ? (const void *)L.pinv64 : (const void *)L.pinv32);
   a.nslots = L.nslots;
   a.omega = omega;
   a.assign = assign ? 1 : 0;
   a.gate = L.gate;
   a.klein = L.klein ? 1 : 0;
   for (int k = 0; k < 20; ++k)
-    for (int l = 0; l < 7; ++l) a.kb[k][l] = sizeof(T) == 8 ? (T)L.kb64[k][l] : (T)L.kb32[k][l];
-  BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
+    for (int l = 0; l < 7; ++l) a.kb[k][l] = sizeof(S) == 8 ? (S)L.kb64[k][l] : (S)L.kb32[k][l];
   // the largest patch tile that still gives every SM about two CTAs; smaller tiles also
   // spread each patch's rows over more threads
   // (two 21-wide shared arrays per patch: 32 x 8 patches take 43 KB in FP32, 87 KB in FP64)
@@ -619,6 +622,18 @@ int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t s
   else if (vanka_ctas(L, 8, 8) >= want) launch_vanka_tile<T, 8, 8, 256>(a, L, st);
   else if (vanka_ctas(L, 8, 4) >= want) launch_vanka_tile<T, 8, 4, 160>(a, L, st);
   else launch_vanka_tile<T, 4, 4, 160>(a, L, st);
+}
+
+template <typename T>
+int launch_vanka_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign) {
+  BMG_PROF_BEGIN(BMG_PROF_VANKA, L.n, st);
+  // FP32 sweep with FP64 patch solves (FP64 inverses, FP64 products) when the level asks
+  if constexpr (sizeof(T) == 4) {
+    if (L.solve64) launch_vanka_sweep_s<T, double>(L, r, x, omega, st, assign);
+    else launch_vanka_sweep_s<T, T>(L, r, x, omega, st, assign);
+  } else {
+    launch_vanka_sweep_s<T, T>(L, r, x, omega, st, assign);
+  }
   BMG_PROF_END(st, (double)L.n * L.n);
   BMG_CHECK_LAUNCH("vanka_sweep_kernel");
   return BMG_OK;

@@ -333,3 +333,32 @@ def test_exact_divdiv_vcycle_parity_and_degradation(bmg, smoother, omega):
         x = torch.zeros_like(b)
         its[dd] = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=1500)["iters"]
     assert its["exact"] >= 2 * its["reduced"], its
+
+
+@pytest.mark.parametrize("kind", ["const", "lognormal"])
+def test_fp32_vcycle_with_fp64_patch_solves(bmg, kind):
+    """FP32 V-cycle whose Vanka patch solves use the FP64 inverses and FP64 products
+    (patch_solve = BMG_PATCH_FP64): against the oracle's FP64 V-cycle within FP32 rounding
+    (1e-5 relative, max-norm), n = 32; and an FGMRES solve with it meets 1e-8."""
+    import torch
+    n = 32
+    p = dict(lam=1e4, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    if kind == "const":
+        kL = kU = None
+        kinvL = kinvU = np.ones((n, n))
+    else:
+        kL, kU = synthetic.lognormal_k(n, 1.0, 14)
+        kinvL, kinvU = 1 / kL, 1 / kU
+    Kf = None if kL is None else kfield(bmg, n, kL, kU)
+    s = bmg.assemble(n, p["lam"], p["mu"], Kf, 1.0, p["tau"], p["alpha"], p["inv_M"])
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, n_coarse=8, precision="fp32", patch_solve="fp64")
+    H = mg.Hierarchy(n, fem.Params(**p), kinvL, kinvU, smoother="vanka", omega=0.7, nu1=1, nu2=1, n_coarse=8)
+    f = synthetic.rhs(n, 15)
+    r = dev(bmg, n, f)
+    z = torch.empty_like(r)
+    h.vcycle(r, z)
+    zo = H.vcycle(H.levels[0].mesh.pack(f))
+    assert relmax(to_oracle(bmg, H.levels[0].mesh, z), zo) < 1e-5
+    x = torch.zeros_like(r)
+    info = h.fgmres_solve(r, x, rtol=1e-8, maxit=400)
+    assert info["status"] == "converged" and info["relres"] <= 1e-8
