@@ -244,6 +244,20 @@ int bmg_adjoint_gradient(const bmg_system *s, const double *x, const double *xi,
                          double *dtheta, double *dlame, void *stream);
 
 /*
+ * bmg_backward_euler_rhs -- right-hand side of one backward-Euler step of Sec. 2.1 (Eqs.
+ * discrete1-3, discrete3 scaled by -1): b = load + [0; 0; alpha B_u u_prev - (1/M) M_p p_prev],
+ * i.e. the pressure rows of A applied to (u_prev, 0, p_prev) added to the step's loads, the
+ * displacement and flux rows being the loads alone.  x_prev is the previous step's solution
+ * (its flux blocks are not read; for the first step a vector holding the initial u and p);
+ * load holds the step's loads in the vector layout, with the pressure rows already carrying
+ * -tau (f, q); b receives the right-hand side (constrained and unused slots zero).  All
+ * device vectors of bmg_vector_len(n) doubles; b may not alias x_prev or load.  A time loop
+ * alternates this call with bmg_fgmres_solve (x_prev as the initial guess).
+ */
+int bmg_backward_euler_rhs(const bmg_system *s, const double *x_prev, const double *load,
+                           double *b, void *stream);
+
+/*
  * Kernel timing (tracing).  bmg_profile_start(kernel, n) makes every later launch of the
  * named kernel family on an n-cell grid (n = 0: any grid) bracket itself with a pair of CUDA
  * events on its own stream; bmg_profile_stop() synchronises those events and returns the

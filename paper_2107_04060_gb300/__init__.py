@@ -63,6 +63,7 @@ _sig = {
     "bmg_assemble_logk": (C.c_int, [C.c_int, C.c_double, C.c_double, _vp, C.c_double, C.c_double,
                                     C.c_double, _vp, C.POINTER(_vp)]),
     "bmg_adjoint_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "bmg_backward_euler_rhs": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "bmg_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
     "bmg_residual": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "bmg_setup_hierarchy": (C.c_int, [_vp, C.POINTER(MgOpts), _vp, C.POINTER(_vp)]),
@@ -186,6 +187,11 @@ class System:
 
     def residual(self, b, x, r, stream=None):
         _check(lib.bmg_residual(self._h, _ptr(b), _ptr(x), _ptr(r), _stream(stream)), "bmg_residual")
+
+    def backward_euler_rhs(self, x_prev, load, b, stream=None):
+        """``bmg_backward_euler_rhs``: b = load + the pressure-row history term of x_prev."""
+        _check(lib.bmg_backward_euler_rhs(self._h, _ptr(x_prev), _ptr(load), _ptr(b), _stream(stream)),
+               "bmg_backward_euler_rhs")
 
     def adjoint_gradient(self, x, xi, dtheta, dlame, stream=None):
         """``bmg_adjoint_gradient``: dtheta (2 blocks, layout of K) and dlame = (dL/dlambda,

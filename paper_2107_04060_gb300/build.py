@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbiotmg.so")
 SOURCES = ["element.cpp", "operator.cu", "vanka.cu", "bsr.cu", "transfer.cu", "coarse.cu",
-           "krylov.cu", "api.cu", "noalloc.cu", "adjoint.cu", "batch.cu"]
+           "krylov.cu", "api.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "timestep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

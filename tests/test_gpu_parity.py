@@ -11,7 +11,8 @@ Tolerances (all relative to the max-norm of the oracle's result):
     condition number amplifies the residual difference).  At lambda/mu = 1e6 the Arnoldi
     estimate and the true residual separate near 1e-7 on both sides (FP64 rounding of the
     lambda B_u^T M_p^{-1} B_u term, amplified by the preconditioner's transient), so the final
-    restart cycle is decided by rounding: there the counts are compared within +-3.
+    restart cycle is decided by rounding: there the counts are compared within +-3, and a
+    separate test compares the iterations to the first true residual below 1e-8 within +-1.
 """
 import numpy as np
 import pytest
@@ -272,3 +273,43 @@ def test_fgmres_long_restart_cycles_agree(bmg):
         s.residual(b, x, r)
         assert (torch.linalg.norm(r) / torch.linalg.norm(b)).item() <= 1.01e-10
     assert (torch.linalg.norm(x1 - x2) / torch.linalg.norm(x2)).item() < 1e-6
+
+
+@pytest.mark.parametrize("smoother,omega", [("vanka", 0.68), ("bsr", 0.68)])
+def test_fgmres_iterations_to_true_residual_at_lambda_1e6(bmg, smoother, omega):
+    """lambda / mu = 1e6 (n = 32), FP64 Arnoldi: a count that does not depend on when the
+    Arnoldi estimate, which separates from the true residual near 1e-7 in FP64 at this
+    lambda, stops the iteration.  Both sides run FGMRES(50) for exactly j iterations (rtol
+    far below reach) and report the true residual of the iterate; the count is the first j
+    whose true relative residual is below 1e-8.  The GPU's and the oracle's counts agree
+    within one."""
+    import torch
+    n = 32
+    p = dict(lam=1e6, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0)
+    s = bmg.assemble(n, 1e6, 1.0, None, 1.0, 1.0, 1.0, 1.0)
+    h = bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8)
+    H = mg.Hierarchy(n, fem.Params(**p), np.ones((n, n)), np.ones((n, n)), smoother=smoother,
+                     omega=omega, omega_J=1.0, n_coarse=8)
+    f = synthetic.rhs(n, 0)
+    b = dev(bmg, n, f)
+    A = H.levels[0].A
+    bo = H.levels[0].mesh.pack(f)
+    x = torch.zeros_like(b)
+    base = h.fgmres_solve(b, x, rtol=1e-8, restart=50, maxit=400)["iters"]
+
+    def first_j(relres_at):
+        for j in range(max(1, base - 12), base + 13):
+            if relres_at(j) <= 1e-8:
+                return j
+        return None
+
+    def gpu_at(j):
+        xg = torch.zeros_like(b)
+        return h.fgmres_solve(b, xg, rtol=1e-15, restart=50, maxit=j)["relres"]
+
+    def oracle_at(j):
+        return krylov.fgmres(A, bo, H.vcycle, rtol=1e-15, restart=50, maxit=j)[1]["relres"]
+
+    jg, jo = first_j(gpu_at), first_j(oracle_at)
+    assert jg is not None and jo is not None, (base, jg, jo)
+    assert abs(jg - jo) <= 1, (jg, jo, base)
