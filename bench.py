@@ -505,17 +505,19 @@ def mixed_workload(n, steps, warmup):
     b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).to(dev)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    x = {p: torch.zeros_like(b) for p in h}
+    x = {p: torch.zeros_like(b) for p in ("fp32", "fp64", "fp32_mixed_arnoldi")}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for p in ("fp32", "fp64"):
+    for p in ("fp32", "fp64", "fp32_mixed_arnoldi"):
+        hp = h["fp32" if p == "fp32_mixed_arnoldi" else p]
+        arn = "mixed" if p == "fp32_mixed_arnoldi" else "fp64"
         for _ in range(warmup):
-            h[p].fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            hp.fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT, arnoldi=arn)
         ms = []
         for _ in range(steps):
             torch.cuda.synchronize()
             ev0.record()
-            info = h[p].fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            info = hp.fgmres_solve(b, x[p], rtol=RTOL, restart=RESTART, maxit=MAXIT, arnoldi=arn)
             ev1.record()
             torch.cuda.synchronize()
             ms.append(ev0.elapsed_time(ev1))
@@ -529,7 +531,9 @@ def mixed_workload(n, steps, warmup):
     res = {"workload": f"mixed precision {n}x{n}, lambda 1e4, lognormal K sigma 2, "
                        "Vanka V(1,1) FGMRES(50) to 1e-8",
            "free_dofs": bmg.free_dofs(n), "fp32_mg": out["fp32"], "fp64": out["fp64"],
+           "fp32_mg_mixed_arnoldi": out["fp32_mixed_arnoldi"],
            "speedup_fp32_vs_fp64": out["fp64"]["ms"] / out["fp32"]["ms"],
+           "speedup_fp32_mixed_arnoldi_vs_fp64": out["fp64"]["ms"] / out["fp32_mixed_arnoldi"]["ms"],
            "error_fp32_mg_vs_fp64": {"rel_2norm": diff, "rel_maxnorm": dmax,
                                      "reference": "the FP64 GPU solution of the same system (parity-tested "
                                                   "against the CPU oracle on smaller grids; the oracle does "
@@ -537,6 +541,48 @@ def mixed_workload(n, steps, warmup):
            "setup_s": setup_s, "steps": steps, "warmup": warmup}
     del h, s
     return res
+
+
+def time_dependent_workload(n, steps, lam=1e4, K=1.0, omega=0.68):
+    """Backward-Euler time stepping (Sec. 2.1, Eqs. discrete1-3), the analogue of Sec. 5.2's
+    runs (average FGMRES iterations per time step): ``steps`` steps of tau = 1/128 on the
+    n x n grid, lambda = 1e4, mu = alpha = 1/M = 1, uniform K, Vanka V(1,1); the loads of step
+    m are exp(-t_m) times a seeded field uniform in [-1, 1], each step's right-hand side is
+    formed on the device (bmg_backward_euler_rhs: loads plus the pressure-row history term)
+    and solved to 1e-8 from the previous step's solution."""
+    import numpy as np
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tau = 1.0 / 128
+    s = bmg.assemble(n, lam, 1.0, None, K, tau, 1.0, INV_M)
+    h = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=omega)
+    f0 = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 7))).to(dev)
+    st = torch.cuda.Stream(device=dev)
+    x = torch.zeros_like(f0)
+    b, ld = torch.empty_like(f0), torch.empty_like(f0)
+    iters = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        torch.cuda.synchronize()
+        ev0.record(st)
+        for m in range(1, steps + 1):
+            torch.mul(f0, float(np.exp(-m * tau)), out=ld)
+            s.backward_euler_rhs(x, ld, b, stream=st)
+            info = h.fgmres_solve(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT, x0_is_zero=False,
+                                  stream=st)
+            if info["status"] != "converged":
+                raise RuntimeError(f"time step {m} did not converge: {info}")
+            iters.append(info["iters"])
+        ev1.record(st)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    return {"workload": f"backward Euler {n}x{n}, {steps} steps of tau = 1/128, lambda {lam:g}, K {K:g}, "
+                        "Vanka V(1,1), seeded loads exp(-t) F, each step to 1e-8 from the previous one",
+            "free_dofs": bmg.free_dofs(n), "steps": steps, "ms_per_step": ms / steps,
+            "value": bmg.free_dofs(n) * steps / (ms * 1e-3) / 1e6, "unit": "MDOF/s (per time step)",
+            "iters_per_step_mean": float(np.mean(iters)), "iters": iters}
 
 
 def run_adjoint(args):
@@ -630,7 +676,7 @@ def main():
     ap.add_argument("--smoother", default="vanka", choices=["vanka", "bsr"], help="--micro vcycle: smoother")
     ap.add_argument("--family", default=None, choices=["apply", "vanka", "vanka_u", "restrict", "prolong"],
                     help="--micro vcycle: kernel family to time (default vanka)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint", "timedep"],
                     help="sweep: the 512^2 parameter sweep (default); batched / mixed / adjoint: "
                          "the batched, 2048^2 mixed-precision and 1024^2 adjoint workloads, each "
                          "printed as its own line")
@@ -670,6 +716,11 @@ def main():
         return
     if args.workload == "adjoint":
         run_adjoint(args)
+        return
+    if args.workload == "timedep":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(time_dependent_workload(args.n, max(1, args.steps))))
         return
 
     import numpy as np
@@ -1100,7 +1151,8 @@ def main():
         wl = {}
         for name, fn in (("mixed_2048", lambda: mixed_workload(args.mixed_n, 1, 1)),
                          ("batched_256", lambda: batched_workload(args.batch_count, 1, 1, True, True)),
-                         ("adjoint_1024", lambda: adjoint_workload(args.adjoint_n, 1, 1, args.fd_dirs))):
+                         ("adjoint_1024", lambda: adjoint_workload(args.adjoint_n, 1, 1, args.fd_dirs)),
+                         ("time_dependent_512", lambda: time_dependent_workload(n, 16))):
             try:
                 t0 = time.perf_counter()
                 wl[name] = fn()
