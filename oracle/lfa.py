@@ -214,7 +214,7 @@ class TwoGrid:
         if smoother == "vanka":
             self._minv = [vanka_entries(prm, kinv, h).symbol(self.theta + np.pi * np.asarray(a, float))
                           for a in HARMONICS]
-        elif smoother == "bsr":
+        elif smoother in ("bsr", "bsr_exact"):
             self._bsr_parts(prm, kinv, h)
         else:
             raise ValueError(smoother)
@@ -237,9 +237,12 @@ class TwoGrid:
                 diagS[t] += v * v / tauDw[s]
         self._tauDw = np.array([tauDw[t] for t in W_IDX])
         self._diagS = np.array([diagS[p] for p in P_IDX])
+        self._c_fs_area = c_fs * area
 
     def _bsr_minv(self, a: int, omega_J: float) -> np.ndarray:
-        """(N, 10, 10) symbol of the inexact BSR operator M^{-1} at harmonic a."""
+        """(N, 10, 10) symbol of the inexact BSR operator M^{-1} at harmonic a (exact BSR when
+        the TwoGrid was made with smoother "bsr_exact": J = S~^{-1} with the symbol
+        S~ = c_fs |T| I + (tau B_w)~ (tau D_w)^{-1} (tau B_w)~^H)."""
         N = len(self.theta)
         L = self.L[a]
         nu, nw = len(U_IDX), len(W_IDX)
@@ -248,7 +251,13 @@ class TwoGrid:
         Fi[:, nu:, nu:] = np.diag(1.0 / self._tauDw)[None]
         B = L[:, P_IDX][:, :, Y_IDX]               # (N, 2, 8)
         BT = L[:, Y_IDX][:, :, P_IDX]              # (N, 8, 2)
-        J = np.diag(omega_J / self._diagS)[None]
+        if self.smoother == "bsr_exact":
+            Bw = L[:, P_IDX][:, :, W_IDX]
+            S = self._c_fs_area * np.eye(len(P_IDX))[None] + Bw @ np.diag(1.0 / self._tauDw)[None] @ \
+                np.conj(np.transpose(Bw, (0, 2, 1)))
+            J = np.linalg.inv(S)
+        else:
+            J = np.diag(omega_J / self._diagS)[None]
         FiBT = Fi @ BT
         JBFi = J @ B @ Fi
         M = np.zeros((N, NT, NT), dtype=complex)
@@ -266,7 +275,7 @@ class TwoGrid:
         N = len(self.theta)
         S = np.zeros((N, 4 * NT, 4 * NT), dtype=complex)
         for a in range(4):
-            Mi = self._minv[a] if self.smoother == "vanka" else self._bsr_minv(a, omega_J)
+            Mi = self._minv[a] if self.smoother == "vanka" else self._bsr_minv(a, omega_J)  # bsr, bsr_exact
             S[:, a * NT:(a + 1) * NT, a * NT:(a + 1) * NT] = np.eye(NT)[None] - omega * (Mi @ self.L[a])
         return S
 

@@ -34,7 +34,7 @@ class Hierarchy:
     def __init__(self, n: int, prm: fem.Params, kinv_L, kinv_U, smoother: str = "vanka",
                  omega: float = 0.8, omega_J: float = 1.0, nu1: int = 1, nu2: int = 1,
                  n_coarse: int = 8, coarse_op: str = "redisc", p_shift: float = 0.0,
-                 w_essential: bool = False, gamma: int = 1):
+                 w_essential: bool = False, gamma: int = 1, bsr_exact: bool = False):
         assert n >= n_coarse and (n // n_coarse) * n_coarse == n
         assert (n // n_coarse) & ((n // n_coarse) - 1) == 0, "n must be n_coarse * 2^k"
         self.prm = prm
@@ -73,7 +73,7 @@ class Hierarchy:
             if smoother == "vanka":
                 L.smoother = Vanka(L.A, L.mesh, omega, p_shift=p_shift)
             elif smoother == "bsr":
-                L.smoother = BraessSarazin(L.A, L.mesh, prm, omega, omega_J)
+                L.smoother = BraessSarazin(L.A, L.mesh, prm, omega, omega_J, exact=bsr_exact)
             else:
                 raise ValueError(smoother)
         c = self.levels[-1]

@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .fem import U_TYPES, W_TYPES, P_TYPES, type_mask
 from .mesh import Mesh
@@ -89,9 +90,14 @@ class Vanka:
 class BraessSarazin:
     """Inexact Braess-Sarazin relaxation with the fixed-stress Schur approximation."""
 
-    def __init__(self, A: sp.csr_matrix, mesh: Mesh, prm, omega: float, omega_J: float):
+    def __init__(self, A: sp.csr_matrix, mesh: Mesh, prm, omega: float, omega_J: float,
+                 exact: bool = False):
+        """``exact=True``: exact Braess-Sarazin (Sec. 3.2.2, Eq. bsr_p solved exactly): the
+        pressure step solves S dp = B z - r_p with a sparse LU of S instead of one weighted
+        Jacobi sweep (omega_J is then unused)."""
         self.omega = float(omega)
         self.omega_J = float(omega_J)
+        self.exact = bool(exact)
         self.mu_ = type_mask(mesh, U_TYPES)
         self.mw_ = type_mask(mesh, W_TYPES)
         self.mp_ = type_mask(mesh, P_TYPES)
@@ -113,6 +119,13 @@ class BraessSarazin:
         Bw2 = self.Bw.multiply(self.Bw).tocsr()
         self.diagS = np.where(self.mp_, c_fs * area, 0.0) + Bw2 @ inv_tauDw
         self.inv_tauDw = inv_tauDw
+        if self.exact:
+            # S = c_fs M_p + tau B_w D_w^{-1} B_w^T on the P0 DoFs
+            pidx = np.nonzero(self.mp_)[0]
+            S = (sp.diags(np.where(self.mp_, c_fs * area, 0.0)) +
+                 self.Bw @ sp.diags(inv_tauDw) @ self.Bw.T).tocsr()[pidx][:, pidx]
+            self.pidx = pidx
+            self.S_lu = spla.splu(S.tocsc())
 
     def F_inv(self, ry: np.ndarray) -> np.ndarray:
         """F^{-1} applied to a vector whose u and w parts are used (p part ignored)."""
@@ -126,7 +139,11 @@ class BraessSarazin:
         rp = np.where(self.mp_, r, 0.0)
         z = self.F_inv(ry)
         Bz = self.Bu @ z + self.Bw @ z
-        dp = np.where(self.mp_, self.omega_J * (Bz - rp) / np.where(self.diagS != 0, self.diagS, 1.0), 0.0)
+        if self.exact:
+            dp = np.zeros_like(r)
+            dp[self.pidx] = self.S_lu.solve((Bz - rp)[self.pidx])
+        else:
+            dp = np.where(self.mp_, self.omega_J * (Bz - rp) / np.where(self.diagS != 0, self.diagS, 1.0), 0.0)
         BTdp = self.Bu.T @ dp + self.Bw.T @ dp
         dy = self.F_inv(ry - BTdp)
         return dy + dp

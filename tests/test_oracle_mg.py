@@ -201,3 +201,48 @@ def test_w_cycle_restores_the_two_grid_factor_for_inexact_bsr():
     w = factor(8, 2)
     assert abs(w - tg) < 0.03
     assert abs(w - 0.687) < 0.03
+
+
+def test_exact_bsr_pressure_step_inverts_the_fixed_stress_schur_complement():
+    """Sec. 3.2.2, Eq. bsr_p with S solved exactly: the exact-BSR correction d = (dy, dp) of a
+    residual r satisfies the block system with the fixed-stress S built here from its
+    definition, (1/M + alpha^2/(lambda + mu)) |T| on the P0 diagonal plus
+    (tau B_w) (tau D_w)^{-1} (tau B_w)^T, with (tau B_w) and tau D_w read off the assembled
+    operator:  F dy + B^T dp = r_y  and  S dp = B F^{-1} r_y - r_p.  F^{-1} is the smoother's
+    displacement/flux solve, taken as a dense matrix from unit vectors.  Inexact BSR (one
+    Jacobi sweep on S) fails the second identity."""
+    n = 4
+    prm = fem.Params(lam=50.0, mu=1.3, tau=0.5, alpha=0.9, inv_M=0.3)
+    m = Mesh(n)
+    kinv = np.linspace(0.5, 2.0, n * n).reshape(n, n)
+    A = fem.assemble(m, prm, kinv, 1.0 / kinv[::-1]).tocsr()
+    fr = np.nonzero(m.free)[0]
+    pm = fem.type_mask(m, fem.P_TYPES)
+    wm = fem.type_mask(m, fem.W_TYPES) & m.free
+    yi = np.array([i for i in fr if not pm[i]])
+    pi = np.nonzero(pm)[0]
+    Ad = A.toarray()
+    B = Ad[np.ix_(pi, yi)]
+    Bw = Ad[np.ix_(pi, np.nonzero(wm)[0])]
+    Dw = np.diag(Ad)[wm]
+    area = 0.5 * m.h ** 2
+    S = (prm.inv_M + prm.alpha ** 2 / (prm.lam + prm.mu)) * area * np.eye(len(pi)) + Bw @ np.diag(1 / Dw) @ Bw.T
+    rng = np.random.default_rng(3)
+    for exact in (True, False):
+        sm = mg.BraessSarazin(A, m, prm, 0.7, 1.0, exact=exact)
+        Finv = np.zeros((len(yi), len(yi)))
+        for c, i in enumerate(yi):
+            e = np.zeros(m.ndof)
+            e[i] = 1.0
+            Finv[:, c] = sm.F_inv(e)[yi]
+        r = np.zeros(m.ndof)
+        r[fr] = rng.standard_normal(len(fr))
+        d = sm.correction(r)
+        dy, dp = d[yi], d[pi]
+        F = np.linalg.inv(Finv)
+        assert np.abs(F @ dy + B.T @ dp - r[yi]).max() <= 1e-9 * np.abs(r).max()
+        err = np.abs(S @ dp - (B @ Finv @ r[yi] - r[pi])).max() / np.abs(S @ dp).max()
+        if exact:
+            assert err <= 1e-10
+        else:
+            assert err > 1e-3
