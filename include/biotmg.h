@@ -62,6 +62,7 @@ extern "C" {
 #define BMG_ERR_ALLOC (-3)    /* device or host allocation failed                      */
 #define BMG_ERR_SINGULAR (-4) /* a patch or coarse-grid factorisation met a zero pivot */
 #define BMG_ERR_NONFINITE (-5)/* non-finite input (right-hand side or coefficients)    */
+#define BMG_ERR_NOCONV (-6)   /* an inner iterative solve missed its tolerance         */
 
 /* ---- solve status (bmg_solve_info.status) ------------------------------------------ */
 #define BMG_CONVERGED 0
@@ -72,6 +73,9 @@ extern "C" {
 /* ---- options ----------------------------------------------------------------------- */
 #define BMG_VANKA 0           /* additive Vanka, 20-DoF vertex patches (Sec. 3.2.1)     */
 #define BMG_BSR 1             /* inexact Braess-Sarazin (Sec. 3.2.2, App. D)            */
+#define BMG_BSR_EXACT 2       /* exact Braess-Sarazin: Eq. bsr_p solved with the fixed-stress
+                                 S (Jacobi-preconditioned CG to 1e-11 relative, FP64 only,
+                                 V-cycles kernel by kernel; BMG_ERR_NOCONV if CG stalls)   */
 #define BMG_FP64 0
 #define BMG_FP32 1
 #define BMG_PATCH_CYCLE 0     /* Vanka patch solves in the V-cycle's precision             */
@@ -141,7 +145,7 @@ int bmg_residual(const bmg_system *s, const double *b, const double *x, double *
                  void *stream);
 
 typedef struct {
-  int smoother;     /* BMG_VANKA or BMG_BSR                                           */
+  int smoother;     /* BMG_VANKA, BMG_BSR or BMG_BSR_EXACT                            */
   int nu1, nu2;     /* pre-/post-relaxation sweeps (>= 0)                             */
   double omega;     /* outer relaxation weight (Sec. 3.2: E_s = I - omega M^{-1} A)    */
   double omega_J;   /* Jacobi weight on the Schur complement (BSR only, App. D)        */
@@ -272,6 +276,7 @@ int bmg_backward_euler_rhs(const bmg_system *s, const double *x_prev, const doub
 #define BMG_PROF_PROLONG 5
 #define BMG_PROF_COARSE 6     /* coarsest-grid solve                                   */
 #define BMG_PROF_KRYLOV 7     /* FGMRES vector kernels (dots, updates, scaling)         */
+#define BMG_PROF_SCHUR 8      /* exact BSR: the Schur-complement CG of one pressure step */
 int bmg_profile_start(int kernel, int n);
 /* Number of kernels this library has launched in the process so far (host-side count; a
  * replayed V-cycle graph counts its kernel nodes). */
@@ -380,6 +385,13 @@ int bmg_hierarchy_levels(const bmg_hierarchy *h);
  * candidate.
  */
 int bmg_hierarchy_tile(const bmg_hierarchy *h, int level, int kernel);
+
+/*
+ * bmg_hierarchy_schur_iters -- exact BSR (smoother BMG_BSR_EXACT): the most conjugate-gradient
+ * iterations one pressure step (Eq. bsr_p) has taken on this hierarchy since setup; 0 before
+ * the first V-cycle, -1 for other smoothers or h = NULL.
+ */
+int bmg_hierarchy_schur_iters(const bmg_hierarchy *h);
 
 void bmg_destroy_system(bmg_system *s);
 void bmg_destroy_hierarchy(bmg_hierarchy *h);

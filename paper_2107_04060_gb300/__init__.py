@@ -25,7 +25,7 @@ if not os.path.exists(LIB_PATH):
 lib = C.CDLL(LIB_PATH)
 
 TYPES = ("ux", "uy", "bh", "bv", "bd", "wh", "wv", "wd", "pL", "pU")
-VANKA, BSR = 0, 1
+VANKA, BSR, BSR_EXACT = 0, 1, 2
 FP64, FP32 = 0, 1
 STATUS = {0: "converged", 1: "maxit", 2: "breakdown", 3: "diverged"}
 
@@ -75,6 +75,7 @@ _sig = {
     "bmg_system_n": (C.c_int, [_vp]),
     "bmg_hierarchy_levels": (C.c_int, [_vp]),
     "bmg_hierarchy_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "bmg_hierarchy_schur_iters": (C.c_int, [_vp]),
     "bmg_destroy_system": (None, [_vp]),
     "bmg_destroy_hierarchy": (None, [_vp]),
     "bmg_status_string": (C.c_char_p, [C.c_int]),
@@ -261,6 +262,10 @@ class Hierarchy:
         """Tile index chosen at setup for a kernel family on a level (``bmg_hierarchy_tile``)."""
         return lib.bmg_hierarchy_tile(self._h, level, PROF[kernel])
 
+    def schur_iters(self) -> int:
+        """Exact BSR: most CG iterations one pressure step took so far (``bmg_hierarchy_schur_iters``)."""
+        return lib.bmg_hierarchy_schur_iters(self._h)
+
     def fgmres_solve(self, b, x, rtol=1e-8, restart=50, maxit=500, x0_is_zero=True, stream=None,
                      arnoldi="fp64"):
         """``bmg_fgmres_solve``; ``arnoldi`` is "fp64" (default) or "mixed"."""
@@ -312,10 +317,11 @@ def setup_hierarchy(system: System, smoother: str = "vanka", nu1: int = 1, nu2: 
                     omega: float = 0.8, omega_J: float = 1.0, n_coarse: int = 8,
                     precision: str = "fp64", p_shift: float = 0.0, cycle: str = "V",
                     coarse_op: str = "redisc", patch_solve: str = "cycle", stream=None) -> Hierarchy:
-    """``bmg_setup_hierarchy``; ``cycle`` is "V" or "W" (gamma = 1 or 2), ``coarse_op``
+    """``bmg_setup_hierarchy``; ``smoother`` is "vanka", "bsr" (inexact Braess-Sarazin) or
+    "bsr_exact" (exact Braess-Sarazin, FP64 only); ``cycle`` is "V" or "W" (gamma = 1 or 2), ``coarse_op``
     "redisc" (the paper's) or "galerkin", ``patch_solve`` "cycle" or "fp64" (FP64 Vanka
     patch solves inside an FP32 V-cycle)."""
-    o = MgOpts(VANKA if smoother == "vanka" else BSR, nu1, nu2, omega, omega_J, n_coarse,
+    o = MgOpts({"vanka": VANKA, "bsr": BSR, "bsr_exact": BSR_EXACT}[smoother], nu1, nu2, omega, omega_J, n_coarse,
                FP64 if precision == "fp64" else FP32, p_shift, {"V": 1, "W": 2}[cycle],
                {"redisc": 0, "galerkin": 1}[coarse_op], {"cycle": 0, "fp64": 1}[patch_solve])
     h = _vp()
@@ -374,7 +380,8 @@ class Batch:
             pass
 
 
-PROF = {"apply": 1, "vanka": 2, "vanka_u": 3, "restrict": 4, "prolong": 5, "coarse": 6, "krylov": 7}
+PROF = {"apply": 1, "vanka": 2, "vanka_u": 3, "restrict": 4, "prolong": 5, "coarse": 6, "krylov": 7,
+        "schur": 8}
 
 
 def noalloc_capacity() -> int:

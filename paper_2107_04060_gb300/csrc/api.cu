@@ -2,6 +2,7 @@
 // Host code only orchestrates: every arithmetic step of assembly, relaxation, transfer,
 // coarse solve and Krylov iteration runs in this library's kernels.
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 #include <chrono>
 #include <cmath>
@@ -91,7 +92,7 @@ static void free_level(Level &L) {
   cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
   cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
   cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2); cudaFree(L.wz);
-  cudaFree(L.bz); cudaFree(L.bd);
+  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.cg); cudaFree(L.cg_flag);
   L = Level();
 }
 
@@ -146,7 +147,7 @@ extern "C" long long bmg_launch_count(void) { return g_launches.load(); }
 extern "C" int bmg_use_graphs(int enable) { return g_use_graphs.exchange(enable ? 1 : 0); }
 
 extern "C" int bmg_profile_start(int kernel, int n) {
-  if (kernel < 1 || kernel > 7 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");
+  if (kernel < 1 || kernel > 8 || n < 0) return arg_error("bmg_profile_start: bad kernel id or n");
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   for (auto e : g_prof.ev) cudaEventDestroy(e);
   g_prof = ProfState();
@@ -195,6 +196,7 @@ extern "C" const char *bmg_status_string(int code) {
     case BMG_ERR_ALLOC: return "allocation failed";
     case BMG_ERR_SINGULAR: return "singular factorisation";
     case BMG_ERR_NONFINITE: return "non-finite or non-positive input";
+    case BMG_ERR_NOCONV: return "inner iterative solve did not converge";
     default: return "unknown status";
   }
 }
@@ -470,8 +472,10 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
   if (!out) return arg_error("bmg_setup_hierarchy: out is NULL");
   *out = nullptr;
   if (!s || !o) return arg_error("bmg_setup_hierarchy: NULL argument");
-  if (o->smoother != BMG_VANKA && o->smoother != BMG_BSR)
+  if (o->smoother != BMG_VANKA && o->smoother != BMG_BSR && o->smoother != BMG_BSR_EXACT)
     return arg_error("bmg_setup_hierarchy: unknown smoother");
+  if (o->smoother == BMG_BSR_EXACT && o->precision != BMG_FP64)
+    return arg_error("bmg_setup_hierarchy: exact BSR runs in FP64 only");
   if (o->precision != BMG_FP64 && o->precision != BMG_FP32)
     return arg_error("bmg_setup_hierarchy: unknown precision");
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 + o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16)
@@ -569,7 +573,10 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
       const PhysParams &p = s->prm;
       const double area = 0.5 / ((double)L.n * L.n);
       const double c_fs = p.inv_M + p.alpha * p.alpha / (p.lambda + p.mu);   // 2 mu / d, d = 2
-      if (!rc) rc = launch_bsr_setup(L, o->omega_J, c_fs * area, st);
+      const bool exact = o->smoother == BMG_BSR_EXACT;     // S solved: 1 / diag(S) unweighted
+      if (!rc) rc = launch_bsr_setup(L, exact ? 1.0 : o->omega_J, c_fs * area, st);
+      L.s_c = c_fs * area;
+      if (!rc && exact) rc = bsr_exact_setup(L, st);
       const size_t vl = vec_len_of(L.n);
       if (!rc && (cudaMalloc(&L.bz, es * vl) != cudaSuccess || cudaMalloc(&L.bd, es * vl) != cudaSuccess))
         rc = cuda_fail(cudaErrorMemoryAllocation, "BSR work vectors");
@@ -599,6 +606,10 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
 }
 
 extern "C" int bmg_hierarchy_levels(const bmg_hierarchy *h) { return h ? (int)h->levels.size() : 0; }
+
+extern "C" int bmg_hierarchy_schur_iters(const bmg_hierarchy *h) {
+  return h && h->opts.smoother == BMG_BSR_EXACT ? h->schur_iters_max : -1;
+}
 
 extern "C" int bmg_hierarchy_tile(const bmg_hierarchy *h, int level, int kernel) {
   if (!h || level < 0 || level >= (int)h->levels.size()) return -1;
@@ -633,6 +644,11 @@ template <typename T>
 static int smooth(bmg_hierarchy *h, const Level &L, const T *r, T *x, cudaStream_t st,
                   bool assign = false) {
   if (h->opts.smoother == BMG_VANKA) return launch_vanka_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);
+  if (h->opts.smoother == BMG_BSR_EXACT) {
+    if constexpr (std::is_same<T, double>::value)
+      return launch_bsr_exact_sweep(L, r, x, h->opts.omega, st, assign, &h->schur_iters_max);
+    return arg_error("exact BSR runs in FP64 only");
+  }
   return launch_bsr_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);
 }
 
@@ -702,7 +718,7 @@ constexpr size_t kMaxVcGraphs = 160;
 
 static int vcycle_any(bmg_hierarchy *h, const double *r, double *z, cudaStream_t st) {
   if (!g_use_graphs.load() || st == nullptr || h->vcycles_direct == 0 || h->graphs_failed ||
-      capturing(st)) {
+      capturing(st) || h->opts.smoother == BMG_BSR_EXACT) {
     ++h->vcycles_direct;
     return vcycle_direct(h, r, z, st);
   }

@@ -149,6 +149,11 @@ struct Level {
   double *sinv64 = nullptr;    // [2][blk] omega_J / diag(S) per triangle
   float *sinv32 = nullptr;
   void *bz = nullptr, *bd = nullptr;   // BSR work vectors
+  // exact BSR: conjugate gradients on S dp = B z - r_p over the two P0 blocks (length 2 blk)
+  double s_c = 0.0;                    // (1/M + alpha^2/(lambda + mu)) |T|
+  double *cg = nullptr;                // r, z, q, p[2] (5 x 2 blk), then the block partials
+  int cg_grid = 0;                     // CTAs of the CG kernels (partials per reduction)
+  int *cg_flag = nullptr;              // device [done, iterations, rr0 valid]
   // coarsest level: dense inverse on the free DoFs
   int nfree = 0;
   int *free_idx = nullptr;     // [nfree] vector positions of the free DoFs
@@ -273,6 +278,7 @@ struct bmg_hierarchy {
   long long vcycles_direct = 0;        // cycles launched kernel by kernel
   bool graphs_failed = false;          // a capture failed: launch kernel by kernel from now on
   int *d_flag = nullptr;       // device error flag (singular pivots)
+  int schur_iters_max = 0;     // exact BSR: most CG iterations one pressure step took
   bmg::Level fine_op;          // the system's fine level with the FP64 operator tile tuned
                                // for this device (FGMRES matvec and true residual)
   // FGMRES workspace (FP64)
@@ -343,6 +349,9 @@ int coarse_setup(Level &L, int *d_flag, cudaStream_t st);
 template <typename T>
 int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st);
 int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st);
+int bsr_exact_setup(Level &L, cudaStream_t st);
+int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double omega, cudaStream_t st,
+                           bool assign, int *iters_max);
 template <typename T>
 int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign);
 // vector kernels

@@ -8,6 +8,8 @@
 // Kernels: (1) z = F^{-1} r_y; (2) dp per triangle; (3) dy = F^{-1}(r_y - B^T dp) fused with
 // the update, r_y - B^T dp formed from the coupling terms of the element products alone
 // (alpha g_T dp_T, tau dw_T dp_T) while the residual is gathered.
+#include <algorithm>
+
 #include "bmg_internal.h"
 #include "kernels_common.cuh"
 
@@ -269,6 +271,7 @@ struct DpArgs {
   const T *sinv;
   const int *gate;
   OpCoefs<T> c;
+  int raw;       // 1: write B z - r_p itself (exact BSR's right-hand side) into d[0 .. 2 blk)
 };
 
 template <typename T>
@@ -294,7 +297,9 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) dz = fma(a.c.dw[0][k], w[k], dz);
     const T Bz = -a.c.alpha * gu - dz;
-    a.d[PL * blk + c00] = a.sinv[c00] * (Bz - a.r[PL * blk + c00]);
+    const T v = Bz - a.r[PL * blk + c00];
+    if (a.raw) a.d[c00] = v;
+    else a.d[PL * blk + c00] = a.sinv[c00] * v;
   }
   {
     const T u[9] = {z[UX * blk + c11], z[UX * blk + c01], z[UX * blk + c10],
@@ -307,7 +312,9 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) dz = fma(a.c.dw[1][k], w[k], dz);
     const T Bz = -a.c.alpha * gu - dz;
-    a.d[PU * blk + c00] = a.sinv[blk + c00] * (Bz - a.r[PU * blk + c00]);
+    const T v = Bz - a.r[PU * blk + c00];
+    if (a.raw) a.d[blk + c00] = v;
+    else a.d[PU * blk + c00] = a.sinv[blk + c00] * v;
   }
 }
 
@@ -382,6 +389,7 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
   a.sinv = (const T *)(f64 ? (const void *)L.sinv64 : (const void *)L.sinv32);
   a.gate = L.gate;
   a.c = *reinterpret_cast<const OpCoefs<T> *>(f64 ? (const void *)&L.c64 : (const void *)&L.c32);
+  a.raw = 0;
   dim3 b(32, 8), gr((L.n + 31) / 32, (L.n + 7) / 8);
   { BMG_PROF_BEGIN(BMG_PROF_VANKA_U, L.n, st);
   BMG_CUDA(launch_pdl(bsr_dp_kernel<T>, dim3(gr), dim3(b), 0, st, a));
@@ -393,5 +401,277 @@ int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st,
 
 template int launch_bsr_sweep<double>(const Level &, const double *, double *, double, cudaStream_t, bool);
 template int launch_bsr_sweep<float>(const Level &, const float *, float *, float, cudaStream_t, bool);
+
+// ---- exact BSR (Sec. 3.2.2: Eq. bsr_p with the fixed-stress S solved, not relaxed) -------
+// S = c I + (tau B_w) (tau D_w)^{-1} (tau B_w)^T on the P0 space, c = (1/M + alpha^2/(lambda +
+// mu)) |T|, is symmetric positive definite; the pressure step runs Jacobi-preconditioned
+// conjugate gradients on it to a relative residual of kCgRtol.  The P0 space is the two
+// triangle blocks (L, U) of blk slots each; cell (i, j) sits at j * pitch + i in both, and the
+// slots outside the n x n cells stay zero in every CG vector.  Per triangle the product is
+//   (S y)_T = c y_T + sum_{edges e of T} (tau B_w)_{T,e} (tau D_w)_e^{-1} sum_{T' on e} (tau B_w)_{T',e} y_T'
+// with the edges d(i,j) (L(i,j), U(i,j)), v(i,j) (L(i,j), U(i-1,j)), h(i,j) (L(i,j), U(i,j-1));
+// boundary edges carry one triangle.  The sign of (tau B_w) cancels in every product.
+//
+// One CG iteration is two kernels over a fixed grid of CTAs (grid-stride over cells):
+//   dir_apply(k): rz_k, rr_k from the previous kernel's per-CTA partials (every CTA sums them
+//                 in the same order, so all see the same scalars); stop test; beta; the new
+//                 direction p_k = z + beta p_{k-1} on the cell and its four neighbours (so no
+//                 CTA waits for another); q = S p_k; partials of p_k . q
+//   update(k):    alpha = rz_k / (p_k . q); x += alpha p_k; r -= alpha q; z = D^{-1} r;
+//                 partials of r . z and r . r
+// Partials, rz and the direction alternate between two slots by iteration parity, so a kernel
+// never overwrites what a CTA of the same launch still reads.  A device flag ends the
+// iteration: the kernels after the stop return at once, and the host reads the flag every
+// kCgCheck iterations.
+constexpr int kCgThreads = 256;
+constexpr double kCgRtol = 1e-11;
+constexpr int kCgMaxIt = 20000;
+constexpr int kCgCheck = 16;
+constexpr int kCgVecs = 5;       // r, z, q, p (two slots)
+
+struct CgArgs {
+  Grid g;
+  double c;
+  double dw[2][3];          // (tau B_w) up to sign, L and U orientation, edges d, v, h
+  const double *dinv;       // [3][blk] 1 / (tau D_w): h, v, d
+  const double *minv;       // [2][blk] 1 / diag(S)
+  double *r, *z, *q, *p[2]; // 2 blk each
+  double *x;                // the p blocks of the BSR work vector (2 blk)
+  double *part;             // [5][grid]: rz (2 parity slots), rr (2), pq
+  double *scal;             // [3]: rz by parity, rr_0
+  int *flag;                // [0] 0 running, 1 converged, 2 non-finite; [1] iterations
+  int k;
+  double tol2;
+};
+
+__device__ __forceinline__ double cg_block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();                     // sh may still be read by a previous call
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < kCgThreads / 32; ++i) t += sh[i];
+  return t;
+}
+
+// The stop flag as one value for the whole CTA (a later CTA of the same launch may see it
+// set by CTA 0; the threads of one CTA must agree before the barriers that follow).
+__device__ __forceinline__ bool cg_stopped(const int *flag) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = *(volatile const int *)flag;
+  __syncthreads();
+  return s != 0;
+}
+
+// sum of the `grid` partials at p, the same value in every CTA
+__device__ __forceinline__ double cg_reduce(const double *p, int grid, double *sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < grid; i += kCgThreads) v += p[i];
+  return cg_block_sum(v, sh);
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const __grid_constant__ CgArgs a) {
+  __shared__ double sh[kCgThreads / 32];
+  const int n = a.g.n, P = a.g.pitch;
+  const size_t blk = a.g.blk;
+  double rz = 0.0, rr = 0.0;
+  for (int c = blockIdx.x * kCgThreads + threadIdx.x; c < n * n; c += gridDim.x * kCgThreads) {
+    const size_t o = (size_t)(c / n) * P + c % n;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const size_t e = t * blk + o;
+      const double r = a.r[e], z = a.minv[e] * r;
+      a.z[e] = z;
+      a.x[e] = 0.0;
+      rz = fma(r, z, rz);
+      rr = fma(r, r, rr);
+    }
+  }
+  const int G = gridDim.x;
+  rz = cg_block_sum(rz, sh);
+  rr = cg_block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    a.part[0 * G + blockIdx.x] = rz;
+    a.part[2 * G + blockIdx.x] = rr;
+    if (blockIdx.x == 0) a.flag[0] = a.flag[1] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_dir_apply_kernel(const __grid_constant__ CgArgs a) {
+  __shared__ double sh[kCgThreads / 32];
+  if (cg_stopped(a.flag)) return;
+  const int G = gridDim.x, k = a.k, par = k & 1;
+  const double rz = cg_reduce(a.part + (0 + par) * G, G, sh);
+  const double rr = cg_reduce(a.part + (2 + par) * G, G, sh);
+  const double rr0 = k == 0 ? rr : a.scal[2];
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (!isfinite(rr) || !isfinite(rz) || rr <= a.tol2 * rr0) {
+    if (lead) {
+      a.flag[0] = isfinite(rr) && isfinite(rz) ? 1 : 2;
+      a.flag[1] = k;
+    }
+    return;
+  }
+  const double beta = k == 0 ? 0.0 : rz / a.scal[par ^ 1];
+  if (lead) {
+    a.scal[par] = rz;
+    if (k == 0) a.scal[2] = rr;
+  }
+  const int n = a.g.n, P = a.g.pitch;
+  const size_t blk = a.g.blk;
+  const double *z = a.z, *po = a.p[par ^ 1];
+  double *pn = a.p[par];
+  // p_k at slot e (k = 0: z alone, the other slot is not read)
+  auto pk = [&](size_t e) { return k == 0 ? z[e] : fma(beta, po[e], z[e]); };
+  const double c = a.c;
+  const double L0 = a.dw[0][0], L1 = a.dw[0][1], L2 = a.dw[0][2];
+  const double U0 = a.dw[1][0], U1 = a.dw[1][1], U2 = a.dw[1][2];
+  double pq = 0.0;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += G * kCgThreads) {
+    const int i = cc % n, j = cc / n;
+    const size_t o = (size_t)j * P + i;
+    const double pL = pk(o), pU = pk(blk + o);
+    const double pUw = i > 0 ? pk(blk + o - 1) : 0.0;        // U(i-1, j)
+    const double pUs = j > 0 ? pk(blk + o - P) : 0.0;        // U(i, j-1)
+    const double pLe = i + 1 < n ? pk(o + 1) : 0.0;          // L(i+1, j)
+    const double pLn = j + 1 < n ? pk(o + P) : 0.0;          // L(i, j+1)
+    const double id = a.dinv[2 * blk + o];                   // d(i, j)
+    const double ivL = a.dinv[1 * blk + o], ivU = a.dinv[1 * blk + o + 1];   // v(i, j), v(i+1, j)
+    const double ihL = a.dinv[0 * blk + o], ihU = a.dinv[0 * blk + o + P];   // h(i, j), h(i, j+1)
+    const double fd = id * fma(L0, pL, U0 * pU);
+    const double qL = c * pL + L0 * fd + L1 * ivL * fma(L1, pL, U1 * pUw) + L2 * ihL * fma(L2, pL, U2 * pUs);
+    const double qU = c * pU + U0 * fd + U1 * ivU * fma(U1, pU, L1 * pLe) + U2 * ihU * fma(U2, pU, L2 * pLn);
+    pn[o] = pL;
+    pn[blk + o] = pU;
+    a.q[o] = qL;
+    a.q[blk + o] = qU;
+    pq = fma(pL, qL, pq);
+    pq = fma(pU, qU, pq);
+  }
+  pq = cg_block_sum(pq, sh);
+  if (threadIdx.x == 0) a.part[4 * G + blockIdx.x] = pq;
+}
+
+__global__ void __launch_bounds__(kCgThreads) cg_update_kernel(const __grid_constant__ CgArgs a) {
+  __shared__ double sh[kCgThreads / 32];
+  if (cg_stopped(a.flag)) return;
+  const int G = gridDim.x, k = a.k, par = k & 1;
+  const double pq = cg_reduce(a.part + 4 * G, G, sh);
+  const double alpha = a.scal[par] / pq;
+  const int n = a.g.n, P = a.g.pitch;
+  const size_t blk = a.g.blk;
+  const double *p = a.p[par];
+  double rz = 0.0, rr = 0.0;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += G * kCgThreads) {
+    const size_t o = (size_t)(cc / n) * P + cc % n;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const size_t e = t * blk + o;
+      a.x[e] = fma(alpha, p[e], a.x[e]);
+      const double r = fma(-alpha, a.q[e], a.r[e]);
+      const double z = a.minv[e] * r;
+      a.r[e] = r;
+      a.z[e] = z;
+      rz = fma(r, z, rz);
+      rr = fma(r, r, rr);
+    }
+  }
+  rz = cg_block_sum(rz, sh);
+  rr = cg_block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    a.part[(0 + (par ^ 1)) * G + blockIdx.x] = rz;
+    a.part[(2 + (par ^ 1)) * G + blockIdx.x] = rr;
+  }
+}
+
+// Work space of the exact pressure step and 1 / diag(S) (sinv with omega_J = 1).
+int bsr_exact_setup(Level &L, cudaStream_t st) {
+  const size_t blk = L.g.blk;
+  const long long cells = (long long)L.n * L.n;
+  L.cg_grid = (int)std::min<long long>((cells + kCgThreads - 1) / kCgThreads, 4 * 152);
+  const size_t len = kCgVecs * 2 * blk + 5 * (size_t)L.cg_grid + 3;
+  BMG_CUDA(cudaMalloc(&L.cg, sizeof(double) * len));
+  BMG_CUDA(cudaMemsetAsync(L.cg, 0, sizeof(double) * len, st));
+  BMG_CUDA(cudaMalloc(&L.cg_flag, sizeof(int) * 2));
+  BMG_CUDA(cudaMemsetAsync(L.cg_flag, 0, sizeof(int) * 2, st));
+  return BMG_OK;
+}
+
+// x <- x + omega (dy, dp) with dp = S^{-1}(B z - r_p) from conjugate gradients.  Runs kernel by
+// kernel with host reads of the stop flag (not capturable into a graph).
+int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double omega, cudaStream_t st,
+                           bool assign, int *iters_max) {
+  if (capturing(st)) {
+    set_error("exact BSR reads its stop flag on the host and cannot be captured into a graph");
+    return BMG_ERR_ARG;
+  }
+  const size_t blk = L.g.blk;
+  double *z = (double *)L.bz;
+  double *d = (double *)L.bd;
+  int rc = launch_vanka_u<double>(L, r, z, nullptr, nullptr, omega, 0, false, st);
+  if (rc) return rc;
+  CgArgs c;
+  c.g = L.g;
+  c.c = L.s_c;
+  for (int o = 0; o < 2; ++o)
+    for (int k = 0; k < 3; ++k) c.dw[o][k] = L.c64.dw[o][k];
+  c.dinv = L.dinv64;
+  c.minv = L.sinv64;
+  c.r = L.cg;
+  c.z = L.cg + 2 * blk;
+  c.q = L.cg + 4 * blk;
+  c.p[0] = L.cg + 6 * blk;
+  c.p[1] = L.cg + 8 * blk;
+  c.x = d + (size_t)PL * blk;
+  c.part = L.cg + kCgVecs * 2 * blk;
+  c.scal = c.part + 5 * (size_t)L.cg_grid;
+  c.flag = L.cg_flag;
+  c.k = 0;
+  c.tol2 = kCgRtol * kCgRtol;
+  BMG_PROF_BEGIN(BMG_PROF_SCHUR, L.n, st);
+  {
+    DpArgs<double> a;
+    a.g = L.g;
+    a.z = z;
+    a.r = r;
+    a.d = c.r;
+    a.sinv = L.sinv64;
+    a.gate = L.gate;
+    a.c = L.c64;
+    a.raw = 1;
+    dim3 b(32, 8), gr((L.n + 31) / 32, (L.n + 7) / 8);
+    BMG_CUDA(launch_pdl(bsr_dp_kernel<double>, dim3(gr), dim3(b), 0, st, a));
+    BMG_CHECK_LAUNCH("bsr_dp_kernel");
+  }
+  const dim3 grid(L.cg_grid), block(kCgThreads);
+  cg_init_kernel<<<grid, block, 0, st>>>(c);
+  BMG_CHECK_LAUNCH("cg_init_kernel");
+  int hflag[2] = {0, 0};
+  for (int k = 0; k < kCgMaxIt; ++k) {
+    c.k = k;
+    cg_dir_apply_kernel<<<grid, block, 0, st>>>(c);
+    BMG_CHECK_LAUNCH("cg_dir_apply_kernel");
+    cg_update_kernel<<<grid, block, 0, st>>>(c);
+    BMG_CHECK_LAUNCH("cg_update_kernel");
+    if ((k + 1) % kCgCheck == 0 || k + 1 == kCgMaxIt) {
+      BMG_CUDA(cudaMemcpyAsync(hflag, L.cg_flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
+      BMG_CUDA(cudaStreamSynchronize(st));
+      if (hflag[0]) break;
+    }
+  }
+  BMG_PROF_END(st, (double)L.n * L.n);
+  if (hflag[0] == 0) {
+    set_error("exact BSR: conjugate gradients on the Schur complement did not reach the tolerance");
+    return BMG_ERR_NOCONV;
+  }
+  if (hflag[0] == 2) {
+    set_error("exact BSR: non-finite residual in the Schur-complement solve");
+    return BMG_ERR_NONFINITE;
+  }
+  if (iters_max && hflag[1] > *iters_max) *iters_max = hflag[1];
+  return launch_vanka_u<double>(L, r, nullptr, x, d, omega, 1, assign, st);
+}
 
 }  // namespace bmg
