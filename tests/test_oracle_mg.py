@@ -7,8 +7,8 @@
   -> rho_N = 0.757.
 * Sec. 4.3: with omega = 0.9 additive Vanka diverges for nu > 0.2 (negative control).
 * Table 4: FGMRES with a four-level V-cycle on the steady manufactured problem (h = 1/64,
-  coarsest h = 1/8, tolerance 1e-6): Vanka at k = 1 needs 9 (nu = 0.4) and 13 (nu = 0.499)
-  iterations.
+  coarsest h = 1/8, tolerance 1e-6): the Vanka counts at nu = 0, 0.4, 0.499 and k = 1 and
+  the smallest k are the printed ones plus one constant offset (3 or 4).
 * Sec. 5.1 / Fig. 5: |u - u_h|_H1 = O(h), ||p - p_h||_L2 = O(h^2), u-errors independent of nu.
 * FGMRES (Sec. 5.1) reaches the direct solution on small grids.
 
@@ -63,22 +63,27 @@ def test_vanka_omega09_diverges_for_large_nu():
 
 @pytest.mark.slow
 def test_table4_iterations_vanka():
-    """Table 4 (Vanka rows, k = 1): 9 iterations at nu = 0.4 and 13 at nu = 0.499.  The
-    oracle reproduces the ordering with an offset of a few iterations (V(2,2) reading; the
-    paper's load quadrature and stopping details are not stated): the pin is the ordering and
-    counts within [paper, paper + 5]."""
-    n, k = 64, 1.0
-    its = {}
-    for nu, om in ((0.4, 0.80), (0.499, 0.72)):
+    """Table 4 (Vanka rows, FGMRES to 1e-6 with a four-level V-cycle, h = 1/64): the oracle
+    reproduces the printed pattern up to one constant offset.  With V(2,2) and Table 2's
+    omega_opt for each (nu, k), the counts over nu in {0, 0.4, 0.499} and k = 1 and the
+    smallest k exceed the paper's by 3 or 4 in every entry (printed 18, 10; 9, 10; 13, 14),
+    so the drop at nu = 0 for k <= 1e-8 (18 -> 10) and the flat rows are reproduced; the
+    offset itself comes from a stopping or scaling detail the paper does not print (a stop on
+    the preconditioned residual or one decade less reduction does not give one constant)."""
+    n = 64
+    cases = [(0.0, 1.0, 0.92, 18), (0.0, 1e-8, 0.88, 10), (0.4, 1.0, 0.80, 9),
+             (0.4, 1e-10, 0.76, 10), (0.499, 1.0, 0.72, 13), (0.499, 1e-10, 0.74, 14)]
+    off = []
+    for nu, k, om, paper in cases:
         prm = paper_params(nu)
         kinv = np.full((n, n), 1.0 / k)
         H = mg.Hierarchy(n, prm, kinv, kinv, smoother="vanka", omega=om, nu1=2, nu2=2, n_coarse=8)
         L = H.levels[0]
         b = manufactured.rhs(L.mesh, prm)
         _, info = krylov.fgmres(L.A, b, H.vcycle, rtol=1e-6, restart=50, maxit=100)
-        its[nu] = info["iters"]
-    assert its[0.4] < its[0.499]
-    assert 9 <= its[0.4] <= 14 and 13 <= its[0.499] <= 18
+        off.append(info["iters"] - paper)
+    assert min(off) >= 2 and max(off) <= 5, off
+    assert max(off) - min(off) <= 1, off
 
 
 def test_convergence_rates():
