@@ -46,10 +46,12 @@ MAXIT_ARM = 300
 # 1.20 TFLOP/s with a register FMA loop), HBM from the measured-peaks file of this GPU model
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per fine-level launch of the FP64 operator inside the sweep, from
-# one ncu capture of the cell-pair kernel, and the SHA-256 prefix of the operator source it
-# was taken with: the bench reports the figure only while that source is unchanged (else
-# null, until the counters are taken again)
-APPLY_TRAFFIC = (42.8e6, "e9b9ef77e8028520")
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, 5 fine-level launches of a
+# single-stream step): the FGMRES matvec y = A z reads x and K^{-1} (25.60 MB, its output
+# stays in L2), the true residual r = b - A x also reads b (46.9 MB); with the SHA-256 prefix
+# of the operator source they were taken with: the bench reports the figure only while that
+# source is unchanged (else null, until the counters are taken again)
+APPLY_TRAFFIC = {"matvec": 25.60e6, "residual": 46.90e6, "digest": "207e32efc592b349"}
 # algorithmic work per grid cell of the fine-level kernels: the operator counts the nonzero
 # products of the element matrices (156 flops per triangle, two triangles per cell, plus 26
 # for the gather and the residual); Vanka: the 20 x 20 inverse (400 FMAs) plus the weighted
@@ -59,8 +61,9 @@ FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 6
 BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208, "restrict": 100, "prolong": 180}
 
 
-def apply_traffic():
-    """The recorded DRAM bytes per operator launch if the operator source still matches."""
+def apply_traffic(n_matvec, n_residual):
+    """Mean recorded DRAM bytes per operator launch over n_matvec FGMRES matvecs and
+    n_residual true residuals, if the operator source still matches."""
     import hashlib
     path = os.path.join(ROOT, "paper_2107_04060_gb300", "csrc", "operator.cu")
     try:
@@ -68,7 +71,9 @@ def apply_traffic():
             digest = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    return APPLY_TRAFFIC[0] if digest == APPLY_TRAFFIC[1] else None
+    if digest != APPLY_TRAFFIC["digest"] or n_matvec + n_residual <= 0:
+        return None
+    return (n_matvec * APPLY_TRAFFIC["matvec"] + n_residual * APPLY_TRAFFIC["residual"]) / (n_matvec + n_residual)
 
 
 # Damping of the V(1,1) cycles at each (lambda, K, 1/M) point of the sweep: the minimisers of
@@ -585,6 +590,42 @@ def time_dependent_workload(n, steps, lam=1e4, K=1.0, omega=0.68):
             "iters_per_step_mean": float(np.mean(iters)), "iters": iters}
 
 
+def bsr_exact_workload(n, lams=(1.0, 1e4, 1e6), Ks=(1.0, 1e-6)):
+    """Exact against inexact Braess-Sarazin (Sec. 3.2.2): the BSR solves of the sweep's
+    (lambda, K) points on the n x n grid, V(1,1) with the sweep's LFA damping, once with the
+    pressure step relaxed by one Jacobi sweep (inexact, the paper's) and once solved by CG on
+    the fixed-stress Schur complement (exact); FGMRES(50) to 1e-8, one solve after the other."""
+    import torch
+    import paper_2107_04060_gb300 as bmg
+    import synthetic
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.Stream(device=dev)
+    cases = [c for c in smoother_cases(INV_M) if c["smoother"] == "bsr"]
+    rows = []
+    with torch.cuda.stream(st):
+        for c in cases:
+            s = bmg.assemble(n, c["lam"], 1.0, None, c["K"], 1.0, 1.0, INV_M)
+            b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, c["seed"]))).to(dev)
+            row = {"lam": c["lam"], "K": c["K"]}
+            for sm in ("bsr", "bsr_exact"):
+                h = bmg.setup_hierarchy(s, sm, 1, 1, omega=c["omega"], omega_J=c["omega_J"], n_coarse=8)
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = h.fgmres_solve(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT, stream=st)
+                torch.cuda.synchronize()
+                row[sm] = {"iters": info["iters"], "status": info["status"],
+                           "s": round(time.perf_counter() - t0, 3)}
+                if sm == "bsr_exact":
+                    row[sm]["cg_iters_max"] = h.schur_iters()
+                del h
+            rows.append(row)
+            del s
+    return {"workload": f"exact vs inexact BSR V(1,1), {n}x{n}, the sweep's BSR points (lambda x K), "
+                        "FGMRES(50) to 1e-8; exact: Jacobi-CG on the fixed-stress S to 1e-11",
+            "free_dofs": bmg.free_dofs(n), "solves": rows}
+
+
 def run_adjoint(args):
     import torch
     torch.cuda.set_device(0)
@@ -676,7 +717,7 @@ def main():
     ap.add_argument("--smoother", default="vanka", choices=["vanka", "bsr"], help="--micro vcycle: smoother")
     ap.add_argument("--family", default=None, choices=["apply", "vanka", "vanka_u", "restrict", "prolong"],
                     help="--micro vcycle: kernel family to time (default vanka)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint", "timedep"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batched", "mixed", "adjoint", "timedep", "bsr_exact"],
                     help="sweep: the 512^2 parameter sweep (default); batched / mixed / adjoint: "
                          "the batched, 2048^2 mixed-precision and 1024^2 adjoint workloads, each "
                          "printed as its own line")
@@ -721,6 +762,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(time_dependent_workload(args.n, max(1, args.steps))))
+        return
+    if args.workload == "bsr_exact":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(bsr_exact_workload(args.n)))
         return
 
     import numpy as np
@@ -1056,10 +1102,12 @@ def main():
         return achieved, avg_ms
     if prof and prof["launches"]:
         achieved, avg_ms = roofline_of(prof)
+        n_mv = sum(r[1]["iters"] for r in recs64)     # one matvec per FGMRES iteration
         out["roofline"] = {"kernel": dominant + "<double> (fine level)", "bound": "alu",
                            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                            "frac": achieved / FP64_PEAK_TFLOPS,
-                           "traffic": apply_traffic() if dominant == "apply" else None,
+                           "traffic": (apply_traffic(n_mv, prof["launches"] - n_mv)
+                                       if dominant == "apply" and graphs_in_timed else None),
                            "avg_launch_ms": avg_ms, "launches": prof["launches"],
                            "peak_source": "nominal FP64 rate of the GB300 (1.25 TFLOP/s; a register-FMA loop measured 1.20)",
                            "timed_region": f"{nstreams} concurrent solves: launches share the GPU",
@@ -1152,7 +1200,8 @@ def main():
         for name, fn in (("mixed_2048", lambda: mixed_workload(args.mixed_n, 1, 1)),
                          ("batched_256", lambda: batched_workload(args.batch_count, 1, 1, True, True)),
                          ("adjoint_1024", lambda: adjoint_workload(args.adjoint_n, 1, 1, args.fd_dirs)),
-                         ("time_dependent_512", lambda: time_dependent_workload(n, 16))):
+                         ("time_dependent_512", lambda: time_dependent_workload(n, 16)),
+                         ("bsr_exact_256", lambda: bsr_exact_workload(256))):
             try:
                 t0 = time.perf_counter()
                 wl[name] = fn()
