@@ -61,6 +61,18 @@ FLOPS_PER_CELL = {"vanka": 2 * 400 + 10, "apply": 2 * 156 + 26, "vanka_u": 2 * 6
 BYTES_PER_CELL_F64 = {"vanka": 240, "apply": 256, "vanka_u": 208, "restrict": 100, "prolong": 180}
 
 
+def vcycle_bytes_per_cell(fam, precision="fp64", per_patch=False, factors_fp64=None):
+    """Algorithmic HBM bytes per grid cell of one fine-level launch: the vectors in the
+    V-cycle's precision, plus, with per-patch factors (varying K), one patch inverse per vertex
+    read once: 210 packed entries (20-DoF Vanka) or 64 (8-DoF displacement Vanka of BSR), in
+    FP64 when ``factors_fp64`` (default: FP64 V-cycles) else FP32."""
+    vec = BYTES_PER_CELL_F64[fam] * (0.5 if precision == "fp32" else 1.0)
+    if not per_patch or fam not in ("vanka", "vanka_u"):
+        return vec
+    f64 = (precision == "fp64") if factors_fp64 is None else factors_fp64
+    return vec + {"vanka": 210, "vanka_u": 64}[fam] * (8 if f64 else 4)
+
+
 def apply_traffic(n_matvec, n_residual):
     """Mean recorded DRAM bytes per operator launch over n_matvec FGMRES matvecs and
     n_residual true residuals, if the operator source still matches."""
@@ -333,7 +345,7 @@ def run_micro(args):
     prof = bmg.profile_stop()
     avg = prof["ms"] / max(prof["launches"], 1)
     cells = prof["cells"] / max(prof["launches"], 1)
-    bpc = BYTES_PER_CELL_F64[fam] * (0.5 if args.precision == "fp32" else 1.0)
+    bpc = vcycle_bytes_per_cell(fam, args.precision, per_patch=not args.uniform_k)
     tiles = None
     if h is not None:
         tiles = {str(n >> l): [h.tile(l, "apply"), h.tile(l, "vanka"), h.tile(l, "vanka_u")]
@@ -341,6 +353,7 @@ def run_micro(args):
     print(json.dumps({"micro": args.micro, "n": n, "precision": args.precision, "uniform_k": args.uniform_k,
                       "residual": args.residual, "tiles_apply_vanka_vankau": tiles,
                       "gbs_algorithmic_this_precision": bpc * cells / (avg * 1e-3) / 1e9,
+                      "bytes_per_cell": bpc,
                       "call_ms": ev0.elapsed_time(ev1) / args.reps, "kernel": fam,
                       "kernel_avg_ms": avg, "launches": prof["launches"],
                       "gflops_fp64": FLOPS_PER_CELL[fam] * cells / (avg * 1e-3) / 1e9,
@@ -494,9 +507,12 @@ def run_mixed(args):
 def mixed_workload(n, steps, warmup):
     """Mixed-precision workload: the n x n grid (2048), lambda = 1e4, mu = 1, per-triangle
     lognormal K (sigma = 2, seed 0), right-hand side seed 0; FGMRES(50) to 1e-8 with FP32
-    V-cycles (FP32 accumulation, FP64 patch factors rounded to FP32) against the same solve
-    with FP64 V-cycles.  Reports per solve the time, iterations and FP64 true residual, and
-    the error of the FP32-MG solution against the FP64 one (2-norm and max-norm, relative)."""
+    V-cycles (FP32 accumulation, FP64 patch factors rounded to FP32; and with the FP64
+    factors and FP64 patch solves) against the same solve with FP64 V-cycles.  Reports per
+    solve the time, iterations and FP64 true residual, the error of the FP32-MG solution
+    against the FP64 one (2-norm and max-norm, relative), and the HBM rate of the FP32
+    V-cycle's fine-level operator and Vanka launches (algorithmic bytes, per-patch factors
+    included, over CUDA-event time, the kernels alone on the GPU)."""
     import numpy as np
     import torch
     import paper_2107_04060_gb300 as bmg
@@ -507,13 +523,16 @@ def mixed_workload(n, steps, warmup):
     t0 = time.perf_counter()
     s = bmg.assemble(n, 1e4, 1.0, K, 0.0, 1.0, 1.0, INV_M)
     h = {p: bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision=p) for p in ("fp32", "fp64")}
+    h["fp32_patch_fp64"] = bmg.setup_hierarchy(s, "vanka", 1, 1, omega=0.7, precision="fp32",
+                                               patch_solve="fp64")
     b = torch.from_numpy(bmg.pack(n, synthetic.rhs(n, 0))).to(dev)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    x = {p: torch.zeros_like(b) for p in ("fp32", "fp64", "fp32_mixed_arnoldi")}
+    runs = ("fp32", "fp64", "fp32_mixed_arnoldi", "fp32_patch_fp64")
+    x = {p: torch.zeros_like(b) for p in runs}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for p in ("fp32", "fp64", "fp32_mixed_arnoldi"):
+    for p in runs:
         hp = h["fp32" if p == "fp32_mixed_arnoldi" else p]
         arn = "mixed" if p == "fp32_mixed_arnoldi" else "fp64"
         for _ in range(warmup):
@@ -533,10 +552,35 @@ def mixed_workload(n, steps, warmup):
                       mdofs=bmg.free_dofs(n) / (float(np.median(ms)) * 1e-3) / 1e6)
     diff = (torch.linalg.norm(x["fp32"] - x["fp64"]) / torch.linalg.norm(x["fp64"])).item()
     dmax = ((x["fp32"] - x["fp64"]).abs().max() / x["fp64"].abs().max()).item()
+    # HBM rate of the FP32 V-cycle's fine-level kernels (V-cycle calls only, graphs off)
+    peak_gbs, peak_src = measured_hbm_gbs()
+    prev = bmg.use_graphs(False)
+    hbm = {"unit": "GB/s algorithmic (vectors in FP32, per-patch factors read once), fine level",
+           "peak_gbs": peak_gbs, "peak_source": peak_src}
+    vin, vout = b.clone(), torch.empty_like(b)
+    for key, hp, fam, f64 in (("apply", h["fp32"], "apply", False), ("vanka", h["fp32"], "vanka", False),
+                              ("vanka_fp64_factors", h["fp32_patch_fp64"], "vanka", True)):
+        hp.vcycle(vin, vout)
+        torch.cuda.synchronize()
+        bmg.profile_start(fam, n)
+        for _ in range(3):
+            hp.vcycle(vin, vout)
+        torch.cuda.synchronize()
+        r_ = bmg.profile_stop()
+        if r_["launches"]:
+            avg = r_["ms"] / r_["launches"]
+            bpc = vcycle_bytes_per_cell(fam, "fp32", per_patch=True, factors_fp64=f64)
+            gbs = bpc * (r_["cells"] / r_["launches"]) / (avg * 1e-3) / 1e9
+            hbm[key] = {"gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 3), "bytes_per_cell": bpc,
+                        "avg_launch_ms": round(avg, 4), "launches": r_["launches"],
+                        "tile": hp.tile(0, fam)}
+    bmg.use_graphs(prev)
     res = {"workload": f"mixed precision {n}x{n}, lambda 1e4, lognormal K sigma 2, "
                        "Vanka V(1,1) FGMRES(50) to 1e-8",
            "free_dofs": bmg.free_dofs(n), "fp32_mg": out["fp32"], "fp64": out["fp64"],
            "fp32_mg_mixed_arnoldi": out["fp32_mixed_arnoldi"],
+           "fp32_mg_patch_fp64": out["fp32_patch_fp64"],
+           "vcycle_hbm": hbm,
            "speedup_fp32_vs_fp64": out["fp64"]["ms"] / out["fp32"]["ms"],
            "speedup_fp32_mixed_arnoldi_vs_fp64": out["fp64"]["ms"] / out["fp32_mixed_arnoldi"]["ms"],
            "error_fp32_mg_vs_fp64": {"rel_2norm": diff, "rel_maxnorm": dmax,

@@ -421,7 +421,7 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
   if (force && *force) {
     L.tile_apply = std::atoi(force);
   } else {
-    rc = pick_tile(&L.tile_apply, 0, sizeof(T) == 4 ? 5 : 4,
+    rc = pick_tile(&L.tile_apply, 0, 7,
                    [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); }, e0, e1, st);
     if (rc) return rc;
   }
@@ -430,7 +430,7 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
   const bool forced = force_s && *force_s;
   if (h->opts.smoother == BMG_VANKA) {
     if (forced) { L.tile_vanka = std::atoi(force_s); return BMG_OK; }
-    return pick_tile(&L.tile_vanka, 0, 4,
+    return pick_tile(&L.tile_vanka, 0, 7,
                      [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
   }
   if (forced) { L.tile_vanka_u = std::atoi(force_s); return BMG_OK; }
@@ -455,7 +455,7 @@ static int tune_hierarchy(bmg_hierarchy *h, cudaStream_t st) {
       rc = cuda_fail(cudaErrorMemoryAllocation, "tuning vectors");
     } else {
       cudaMemsetAsync(a, 0, sizeof(double) * vl, st);
-      rc = pick_tile(&F.tile_apply, 0, 4, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
+      rc = pick_tile(&F.tile_apply, 0, 7, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
                      e0, e1, st);
     }
     cudaStreamSynchronize(st);

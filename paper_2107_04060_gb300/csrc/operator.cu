@@ -298,8 +298,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
   }
 }
 
-template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE>
-__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+// MINB > 1 caps the registers so that MINB CTAs fit on an SM (more warps to hide the loads
+// and the barrier, at the price of a few spilled values): tuning candidates.
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
   pdl_enter();
   BMG_GATE(a.gate);
   extern __shared__ unsigned char smem_raw[];
@@ -486,7 +488,7 @@ void free_apply_tma(Level &L) {
   L.tma = nullptr;
 }
 
-template <typename T, int WM, int TX, int TY, int NT, bool DENSE>
+template <typename T, int WM, int TX, int TY, int NT, bool DENSE, int MINB = 1>
 static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   dim3 block(NT);
   dim3 grid((L.g.pitch + TX - 1) / TX, (L.n + 1 + TY - 1) / TY, batch);
@@ -494,12 +496,12 @@ static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, c
   if (smem > 48 * 1024) {
     static bool attr = false;
     if (!attr) {
-      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT, DENSE>,
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT, DENSE, MINB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr = true;
     }
   }
-  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT, DENSE>, dim3(grid), dim3(block), smem, st, a));
+  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT, DENSE, MINB>, dim3(grid), dim3(block), smem, st, a));
   return BMG_OK;
 }
 
@@ -523,6 +525,8 @@ static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cud
             if (L.tma->xptr[k] == (const void *)a.x) return launch_apply_tma<WM>(a, L, L.tma->x[k], st);
       }
       return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
+    case 6: return launch_apply_tile<T, WM, 32, 8, 256, D, 4>(a, L, batch, st);   // 4 CTAs / SM
+    case 7: return launch_apply_tile<T, WM, 16, 8, 128, D, 8>(a, L, batch, st);   // 8 CTAs / SM
     default: break;
   }
   // the largest tile that still gives every SM about two CTAs

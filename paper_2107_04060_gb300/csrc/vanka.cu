@@ -356,9 +356,32 @@ struct VankaSweepArgs {
   S kb[20][7];
 };
 
+// Dense patch solve x = A_slot^{-1} r by one thread from the packed symmetric inverse in
+// global memory: every entry (row, c), c >= row, is loaded once and used for both x[row] and
+// x[c] (210 loads, 400 FMAs, entry-major layout: consecutive patches' loads coalesce).
+template <typename S>
+__device__ __forceinline__ void patch_solve_packed(const S *__restrict__ inv, size_t ld, const S (&r)[20],
+                                                   S (&x)[20]) {
+#pragma unroll
+  for (int c = 0; c < 20; ++c) x[c] = S(0);
+  static_for<20>([&](auto row_) {
+    constexpr int row = decltype(row_)::value;
+    static_for<20 - row>([&](auto d_) {
+      constexpr int c = row + decltype(d_)::value;
+      constexpr int e = row * 20 - (row * (row - 1)) / 2 + (c - row);
+      const S f = __ldg(inv + (size_t)e * ld);
+      x[row] = fma(f, r[c], x[row]);
+      if constexpr (c != row) x[c] = fma(f, r[row], x[c]);
+    });
+  });
+}
+
 // kKlein = false compiles the symmetry-adapted path out (slot-0 patches then use the dense
 // inverse, which is always stored): fewer registers where that path is not used.
-template <typename T, int kPX, int kPY, int NT, bool kKlein = true, typename S = T>
+// kPatchThread: every patch is solved by the thread that gathered its residual, in registers
+// (symmetry-adapted for slot 0 when available, else patch_solve_packed), so the (row, patch)
+// tasks of phase 2 are skipped: the per-patch factors stream through once per patch.
+template <typename T, int kPX, int kPY, int NT, bool kKlein = true, typename S = T, bool kPatchThread = false>
 __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T, S> &a, int bx, int by) {
   constexpr int NP = kPX * kPY, LD = 21;          // LD: padded row of the shared arrays
   // dynamic shared memory (vanka_smem_bytes): residuals sr[NP][LD], corrections sx[NP][LD],
@@ -413,7 +436,32 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T, S> &a, int bx
       for (int c = 0; c < 20; ++c) r[c] = T(0);
     }
     ss[p] = sl;
-    if constexpr (!kKlein) {
+    if constexpr (kPatchThread) {
+      S rs[20], x[20];
+#pragma unroll
+      for (int c = 0; c < 20; ++c) rs[c] = (S)r[c];
+      if (pi > n || pj > n) {
+#pragma unroll
+        for (int c = 0; c < 20; ++c) x[c] = S(0);
+      } else if (kKlein && kl && sl == 0) {
+        S q[20], xq[20];
+        klein_fwd(rs, q);
+        static_for<20>([&](auto k_) {
+          constexpr int k = decltype(k_)::value, b0 = klein_block_start(k);
+          S acc = 0;
+          static_for<klein_block_size(k)>([&](auto l_) {
+            constexpr int l = decltype(l_)::value;
+            acc = fma(a.kb[k][l], q[b0 + l], acc);
+          });
+          xq[k] = acc;
+        });
+        klein_inv(xq, x);
+      } else {
+        patch_solve_packed<S>(a.inv + sl, (size_t)a.nslots, rs, x);
+      }
+#pragma unroll
+      for (int c = 0; c < 20; ++c) sx[p * LD + c] = (T)x[c];
+    } else if constexpr (!kKlein) {
 #pragma unroll
       for (int c = 0; c < 20; ++c) sr[p * LD + c] = r[c];
       if (sl != 0) s_mixed = 1;
@@ -442,7 +490,9 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T, S> &a, int bx
   }
   __syncthreads();
   const size_t ld = (size_t)a.nslots;
-  if (kl) {
+  if constexpr (kPatchThread) {
+    // every patch was solved in phase 1
+  } else if (kl) {
     // the tile's other patches (boundary patches with their own inverses)
     if (s_mixed) {
 #pragma unroll 2
@@ -545,11 +595,11 @@ __device__ __forceinline__ void vanka_tile(const VankaSweepArgs<T, S> &a, int bx
   }
 }
 
-template <typename T, int kPX, int kPY, int NT, typename S>
+template <typename T, int kPX, int kPY, int NT, typename S, bool kPatchThread = false>
 __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__ VankaSweepArgs<T, S> a) {
   pdl_enter();
   BMG_GATE(a.gate);
-  vanka_tile<T, kPX, kPY, NT, true, S>(a, blockIdx.x, blockIdx.y);
+  vanka_tile<T, kPX, kPY, NT, true, S, kPatchThread>(a, blockIdx.x, blockIdx.y);
 }
 
 // Batched form: blockIdx.z selects one of several instances of one grid size; their
@@ -566,19 +616,19 @@ constexpr size_t vanka_smem_bytes() {
   return 2 * (size_t)PX * PY * 21 * sizeof(T) + (size_t)PX * PY * sizeof(int);
 }
 
-template <typename T, int PX, int PY, int NT, typename S>
+template <typename T, int PX, int PY, int NT, typename S, bool PT = false>
 static void launch_vanka_tile(const VankaSweepArgs<T, S> &a, const Level &L, cudaStream_t st) {
   constexpr size_t smem = vanka_smem_bytes<T, PX, PY>();
   static_assert(smem <= 200 * 1024, "shared memory of a Vanka tile");
   if constexpr (smem > 48 * 1024) {
     static const bool opted_in = [] {          // once per instantiation, thread-safe
-      return cudaFuncSetAttribute(vanka_sweep_kernel<T, PX, PY, NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem) == cudaSuccess;
+      return cudaFuncSetAttribute(vanka_sweep_kernel<T, PX, PY, NT, S, PT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
     }();
     (void)opted_in;
   }
   dim3 grid((L.g.pitch + PX - 2) / (PX - 1), (L.n + 1 + PY - 2) / (PY - 1));
-  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT, S>, dim3(grid), dim3(NT), smem, st, a);
+  (void)launch_pdl(vanka_sweep_kernel<T, PX, PY, NT, S, PT>, dim3(grid), dim3(NT), smem, st, a);
 }
 
 static long long vanka_ctas(const Level &L, int px, int py) {
@@ -605,13 +655,18 @@ static void launch_vanka_sweep_s(const Level &L, const T *r, T *x, T omega, cuda
   // (two 21-wide shared arrays per patch: 32 x 8 patches take 43 KB in FP32, 87 KB in FP64)
   const long long want = 2 * 152;
   bool done = true;
-  // tuned at setup: 0 = 32 x 8, 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 patches
+  // tuned at setup: 0 = 32 x 8, 1 = 16 x 8, 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 patches with
+  // (row, patch) solve tasks; 5 = 32 x 8, 6 = 16 x 8, 7 = 8 x 8 patches with one thread per
+  // patch solve
   switch (L.tile_vanka) {
     case 0: launch_vanka_tile<T, 32, 8, 256>(a, L, st); break;
     case 1: launch_vanka_tile<T, 16, 8, 256>(a, L, st); break;
     case 2: launch_vanka_tile<T, 8, 8, 256>(a, L, st); break;
     case 3: launch_vanka_tile<T, 8, 4, 160>(a, L, st); break;
     case 4: launch_vanka_tile<T, 4, 4, 160>(a, L, st); break;
+    case 5: launch_vanka_tile<T, 32, 8, 256, S, true>(a, L, st); break;
+    case 6: launch_vanka_tile<T, 16, 8, 128, S, true>(a, L, st); break;
+    case 7: launch_vanka_tile<T, 8, 8, 64, S, true>(a, L, st); break;
     default: done = false;
   }
   if constexpr (sizeof(T) == 4) {

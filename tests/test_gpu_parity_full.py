@@ -49,11 +49,12 @@ def relmax(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def setup_forced(bmg, s, smoother, omega, tile, **kw):
-    """GPU hierarchy with operator and smoother tiles forced to ``tile`` on every level."""
+def setup_forced(bmg, s, smoother, omega, tile, apply_tile=None, **kw):
+    """GPU hierarchy with the smoother tile forced to ``tile`` and the operator tile to
+    ``apply_tile`` (default: ``tile``) on every level."""
     old = {k: os.environ.get(k) for k in ("BMG_FORCE_APPLY_TILE", "BMG_FORCE_SMOOTHER_TILE")}
     try:
-        os.environ["BMG_FORCE_APPLY_TILE"] = str(tile)
+        os.environ["BMG_FORCE_APPLY_TILE"] = str(tile if apply_tile is None else apply_tile)
         os.environ["BMG_FORCE_SMOOTHER_TILE"] = str(tile)
         return bmg.setup_hierarchy(s, smoother, 1, 1, omega=omega, omega_J=1.0, n_coarse=8, **kw)
     finally:
@@ -72,7 +73,8 @@ CASES = [("vanka", 0.8, "const"), ("vanka", 0.7, "lognormal"), ("bsr", 0.7, "con
 def test_vcycle_parity_every_tile_n128(bmg, smoother, omega, kind):
     """n = 128 (five levels down to 8): every tile candidate of the operator and of the
     smoother, constant coefficients (symmetry-adapted interior Vanka solve) and lognormal K
-    (per-patch inverses)."""
+    (per-patch inverses); the register-capped operator tiles 6 and 7, and Vanka's
+    one-thread-per-patch candidates 5-7 with the 32 x 8 operator tile."""
     import torch
     n = 128
     p = dict(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0) if kind == "const" else \
@@ -90,14 +92,17 @@ def test_vcycle_parity_every_tile_n128(bmg, smoother, omega, kind):
     f = synthetic.rhs(n, 5)
     zo = H.vcycle(H.levels[0].mesh.pack(f))
     r = dev(bmg, n, f)
-    for tile in range(5):
-        h = setup_forced(bmg, s, smoother, omega, tile)
+    combos = [(t, t) for t in range(5)] + [(0, 6), (1, 7)]        # (smoother, operator)
+    if smoother == "vanka":
+        combos += [(5, 0), (6, 0), (7, 0)]
+    for tile, at in combos:
+        h = setup_forced(bmg, s, smoother, omega, tile, apply_tile=at)
         key = "vanka" if smoother == "vanka" else "vanka_u"
-        assert all(h.tile(l, key) == tile and h.tile(l, "apply") == tile for l in range(h.levels - 1))
+        assert all(h.tile(l, key) == tile and h.tile(l, "apply") == at for l in range(h.levels - 1))
         z = torch.empty_like(r)
         h.vcycle(r, z)
         err = relmax(to_oracle(bmg, H.levels[0].mesh, z), zo)
-        assert err < 1e-9, (tile, err)
+        assert err < 1e-9, (tile, at, err)
         h.close()
 
 
@@ -362,3 +367,25 @@ def test_fp32_vcycle_with_fp64_patch_solves(bmg, kind):
     x = torch.zeros_like(r)
     info = h.fgmres_solve(r, x, rtol=1e-8, maxit=400)
     assert info["status"] == "converged" and info["relres"] <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_patch_thread_vanka_matches_row_tasks(bmg, precision):
+    """The one-thread-per-patch Vanka solve (tiles 5-7) accumulates every output in the same
+    order as the (row, patch) tasks (tiles 0-2), so the V-cycles agree to rounding (asserted:
+    1e-6 relative in FP32, 1e-12 in FP64), n = 256, lognormal K (per-patch inverses)."""
+    import torch
+    n = 256
+    kL, kU = synthetic.lognormal_k(n, 2.0, 11)
+    s = bmg.assemble(n, 1e4, 1.0, kfield(bmg, n, kL, kU), 1.0, 1.0, 1.0, 1.0)
+    r = dev(bmg, n, synthetic.rhs(n, 12))
+    tol = 1e-6 if precision == "fp32" else 1e-12
+    for a, b in ((0, 5), (1, 6), (2, 7)):
+        z = []
+        for tile in (a, b):
+            h = setup_forced(bmg, s, "vanka", 0.7, tile, apply_tile=0, precision=precision)
+            zz = torch.empty_like(r)
+            h.vcycle(r, zz)
+            z.append(zz.cpu().numpy())
+            h.close()
+        assert relmax(z[1], z[0]) <= tol, (a, b, relmax(z[1], z[0]))
