@@ -1043,6 +1043,25 @@ def main():
                               "s": round(time.perf_counter() - t0, 3)}
                 del hp
             probe64.append(row)
+    # per solve of the FP32-MG arm: the FP32-MG solution against the FP64-V-cycle solution of
+    # the same system (relative 2-norm), and the FP64 true residual of the FP32-MG solution
+    err32 = None
+    if "fp32" in precisions and not args.no_arms:
+        err32 = []
+        for ci in fp32_cases:
+            c = cases[ci]
+            xa, xb = torch.zeros_like(rhs[c["seed"]]), torch.zeros_like(rhs[c["seed"]])
+            with torch.cuda.stream(streams[0]):
+                hier["fp32", ci].fgmres_solve(rhs[c["seed"]], xa, rtol=RTOL, restart=RESTART, maxit=MAXIT,
+                                              stream=streams[0])
+                hier["fp64", ci].fgmres_solve(rhs[c["seed"]], xb, rtol=RTOL, restart=RESTART, maxit=MAXIT,
+                                              stream=streams[0])
+                rr = torch.empty_like(xa)
+                systems[c["lam"], c["K"]].residual(rhs[c["seed"]], xa, rr, stream=streams[0])
+            torch.cuda.synchronize()
+            err32.append({"lam": c["lam"], "K": c["K"], "smoother": c["smoother"],
+                          "rel_err_vs_fp64": float(f"{(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb)).item():.3g}"),
+                          "true_relres": float(f"{(torch.linalg.norm(rr) / torch.linalg.norm(rhs[c['seed']])).item():.3g}")})
     # the same 12 FP64 solves with the mixed-precision Arnoldi (FP32 first Gram-Schmidt pass,
     # double-float second pass and correction)
     arm_steps = max(1, min(args.steps, 5))
@@ -1134,6 +1153,7 @@ def main():
                           "fp64_same_solves": {"value": sub_dofs / (ms64s * 1e-3) / 1e6, "ms_per_step": ms64s},
                           "speedup_vs_fp64": ms64s / ms32,
                           "iters": [r[1]["iters"] for r in recs32[:len(fp32_cases)]],
+                          "per_solve_vs_fp64": err32,
                           "lambda_1e6_probe": probe64,
                           "vcycle_hbm": {"unit": "GB/s algorithmic, fine level, FP32 V-cycles of the 8 "
                                                  "hierarchies (3 each) alone on the GPU",

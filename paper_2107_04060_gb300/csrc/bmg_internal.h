@@ -215,7 +215,7 @@ constexpr int kAdjBlocks = 152 * 8;   // CTAs of the adjoint-gradient reduction
 // ---- batched launches: one kernel over several instances of one grid size -------------
 // The per-instance arguments (vectors, coefficients, inverse tables, gate) sit in a device
 // array; blockIdx.z (blockIdx.y for the coarse solve) selects the instance.  FP64 only.
-constexpr int kApplyTiles = 5, kVankaTiles = 4;
+constexpr int kApplyTiles = 5, kVankaTiles = 6;
 size_t apply_args_bytes();
 void make_apply_args(const Level &L, const double *x, const double *b, double *y, bool residual,
                      const int *gate, void *dst);

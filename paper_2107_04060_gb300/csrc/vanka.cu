@@ -604,11 +604,11 @@ __global__ void __launch_bounds__(NT) vanka_sweep_kernel(const __grid_constant__
 
 // Batched form: blockIdx.z selects one of several instances of one grid size; their
 // arguments (vectors, inverse tables, damping, gate) are read from a device array.
-template <int kPX, int kPY, int NT>
+template <int kPX, int kPY, int NT, bool kPatchThread = false>
 __global__ void __launch_bounds__(NT) vanka_batch_kernel(const VankaSweepArgs<double> *__restrict__ args) {
   const VankaSweepArgs<double> &a = args[blockIdx.z];
   BMG_GATE(a.gate);
-  vanka_tile<double, kPX, kPY, NT, false>(a, blockIdx.x, blockIdx.y);
+  vanka_tile<double, kPX, kPY, NT, false, double, kPatchThread>(a, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, int PX, int PY>
@@ -717,36 +717,40 @@ void make_vanka_args(const Level &L, const double *r, double *x, double omega, b
   std::memcpy(dst, &a, sizeof(a));
 }
 
-template <int PX, int PY, int NT>
+template <int PX, int PY, int NT, bool PT = false>
 static int launch_vanka_batch_tile(const void *d_args, int count, int n, cudaStream_t st) {
   constexpr size_t smem = vanka_smem_bytes<double, PX, PY>();
   static_assert(smem <= 48 * 1024, "batched tiles stay within the default shared memory");
   const Grid g = grid_of(n);
   dim3 grid((g.pitch + PX - 2) / (PX - 1), (n + 1 + PY - 2) / (PY - 1), count);
-  vanka_batch_kernel<PX, PY, NT><<<grid, NT, smem, st>>>((const VankaSweepArgs<double> *)d_args);
+  vanka_batch_kernel<PX, PY, NT, PT><<<grid, NT, smem, st>>>((const VankaSweepArgs<double> *)d_args);
   BMG_CHECK_LAUNCH("vanka_batch_kernel");
   return BMG_OK;
 }
 
-// tile t: 0 = 16 x 8, 1 = 8 x 8, 2 = 8 x 4, 3 = 4 x 4 patches
+// tile t: 0 = 16 x 8, 1 = 8 x 8, 2 = 8 x 4, 3 = 4 x 4 patches with (row, patch) solve tasks;
+// 4 = 16 x 8, 5 = 8 x 8 patches with one thread per patch solve (autotuning candidates)
 int launch_vanka_batch(const void *d_args, int count, int n, int tile, cudaStream_t st) {
   if (count <= 0) return BMG_OK;
   switch (tile) {
     case 0: return launch_vanka_batch_tile<16, 8, 256>(d_args, count, n, st);
     case 1: return launch_vanka_batch_tile<8, 8, 256>(d_args, count, n, st);
     case 2: return launch_vanka_batch_tile<8, 4, 160>(d_args, count, n, st);
+    case 4: return launch_vanka_batch_tile<16, 8, 128, true>(d_args, count, n, st);
+    case 5: return launch_vanka_batch_tile<8, 8, 64, true>(d_args, count, n, st);
     default: return launch_vanka_batch_tile<4, 4, 160>(d_args, count, n, st);
   }
 }
 
 int default_vanka_tile(int n, int count) {
-  static const int px[kVankaTiles] = {16, 8, 8, 4}, py[kVankaTiles] = {8, 8, 4, 4};
+  constexpr int kRule = 4;                 // the rule picks among the (row, patch) task tiles
+  static const int px[kRule] = {16, 8, 8, 4}, py[kRule] = {8, 8, 4, 4};
   const Grid g = grid_of(n);
-  for (int t = 0; t + 1 < kVankaTiles; ++t) {
+  for (int t = 0; t + 1 < kRule; ++t) {
     const long long c = (long long)((g.pitch + px[t] - 2) / (px[t] - 1)) * ((n + 1 + py[t] - 2) / (py[t] - 1)) * count;
     if (c >= 2 * 152) return t;
   }
-  return kVankaTiles - 1;
+  return kRule - 1;
 }
 
 }  // namespace bmg
