@@ -436,7 +436,8 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
 }
 // Last Gram-Schmidt correction: w <- w - V h (h the second pass's coefficients), with the
 // product V h formed in double-float arithmetic on the FP32 pipe from the FP64 basis (each
-// value split exactly into head and tail, see split_f64 / df_dot_step), fused with the
+// value split into head and tail to about 2^-47 relative, the six lowest mantissa bits
+// dropped; see split_f64 / df_dot_step), fused with the
 // block-partial sums of w.w (FP64).  The product is accurate to about 2^-46 of
 // sum_q |h_q V_q|, so what is subtracted is V h to well below FP64 rounding of w: the
 // Hessenberg column h1 + h2 describes the update exactly, whatever the accuracy of the
