@@ -378,12 +378,13 @@ int bmg_hierarchy_levels(const bmg_hierarchy *h);
  * 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 output positions (Vanka: patches),
  * 5 = FP32 operator, 32 x 8 with its input staged in shared memory by TMA bulk tensor
  * copies (FP64: the 32 x 8 tile), 6 = 32 x 8 and 7 = 16 x 8 operator tiles with registers
- * capped for 4 and 8 CTAs per SM; Vanka 5 = 32 x 8, 6 = 16 x 8, 7 = 8 x 8 patches solved one patch per thread
+ * capped for 4 and 8 CTAs per SM; Vanka and displacement Vanka 5 = 32 x 8, 6 = 16 x 8,
+ * 7 = 8 x 8 patches solved one patch per thread
  * (each packed inverse entry loaded once) instead of (row, patch) tasks.  -1: not tuned or
  * no such level.  The choice does not change any result.  Setting
  * the environment variable BMG_FORCE_APPLY_TILE to one of these indices before
  * bmg_setup_hierarchy fixes the operator's choice on every level; BMG_FORCE_SMOOTHER_TILE
- * (0-7 for Vanka, 0-4 for BSR) fixes the Vanka tile (Vanka hierarchies) or the displacement-Vanka tile (BSR) the
+ * (0-7) fixes the Vanka tile (Vanka hierarchies) or the displacement-Vanka tile (BSR) the
  * same way.  Out-of-range values select the built-in rule.  Both exist to test every
  * candidate.
  */

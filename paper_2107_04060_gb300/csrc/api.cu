@@ -434,7 +434,7 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
                      [&] { return launch_vanka_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
   }
   if (forced) { L.tile_vanka_u = std::atoi(force_s); return BMG_OK; }
-  return pick_tile(&L.tile_vanka_u, 0, 4,
+  return pick_tile(&L.tile_vanka_u, 0, 7,
                    [&] { return launch_bsr_sweep<T>(L, r, z, (T)h->opts.omega, st, false); }, e0, e1, st);
 }
 

@@ -143,7 +143,10 @@ __device__ __forceinline__ T dp_at(const VankaUArgs<T> &a, int b, int ci, int cj
 
 // kQX x kQY patches per CTA, NT threads; outputs (kQX - 1) x (kQY - 1).  Same three phases
 // as the 20-DoF sweep: residual gather, (patch, row) solve tasks, weighted gather.
-template <typename T, int kQX, int kQY, int NT>
+// kPT: the thread that gathers a patch's residual also solves it (64 FMAs, each inverse
+// entry loaded once per patch, in the order of the row tasks' sums), and the task phase is
+// skipped.
+template <typename T, int kQX, int kQY, int NT, bool kPT = false>
 __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ VankaUArgs<T> a) {
   pdl_enter();
   BMG_GATE(a.gate);
@@ -197,10 +200,24 @@ __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ Van
       for (int c = 0; c < 8; ++c) rl[c] = T(0);
       ss[p] = 0;
     }
+    if constexpr (kPT) {
+      T r[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) r[c] = rl[c];
+      const T *inv = a.inv + ss[p];
+      const size_t ld = (size_t)a.nslots;
+#pragma unroll
+      for (int row = 0; row < 8; ++row) {
+        T acc = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc = fma(__ldg(inv + (size_t)(row * 8 + c) * ld), r[c], acc);
+        sx[p * LD + row] = acc;
+      }
+    }
   }
   __syncthreads();
   const size_t ld = (size_t)a.nslots;
-  for (int t = tid; t < NP * 8; t += NT) {
+  for (int t = tid; t < (kPT ? 0 : NP * 8); t += NT) {
     const int row = t / NP, p = t % NP;
     const T *inv = a.inv + ss[p] + (size_t)(row * 8) * ld;
     const T *rl = sr + p * LD;
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(NT) vanka_u_kernel(const __grid_constant__ Van
     for (int c = 0; c < 8; ++c) acc = fma(inv[(size_t)c * ld], rl[c], acc);
     sx[p * LD + row] = acc;
   }
-  __syncthreads();
+  if constexpr (!kPT) __syncthreads();
   for (int q = tid; q < (kQX - 1) * (kQY - 1); q += NT) {
     const int i = i0 + q % (kQX - 1), j = j0 + q / (kQX - 1);
     if (j > n) continue;
@@ -318,10 +335,10 @@ __global__ void bsr_dp_kernel(const __grid_constant__ DpArgs<T> a) {
   }
 }
 
-template <typename T, int QX, int QY, int NT>
+template <typename T, int QX, int QY, int NT, bool PT = false>
 static void launch_vanka_u_tile(const VankaUArgs<T> &a, const Level &L, cudaStream_t st) {
   dim3 grid((L.g.pitch + QX - 2) / (QX - 1), (L.n + 1 + QY - 2) / (QY - 1));
-  (void)launch_pdl(vanka_u_kernel<T, QX, QY, NT>, dim3(grid), dim3(NT), 0, st, a);
+  (void)launch_pdl(vanka_u_kernel<T, QX, QY, NT, PT>, dim3(grid), dim3(NT), 0, st, a);
 }
 
 template <typename T>
@@ -360,6 +377,9 @@ static int launch_vanka_u(const Level &L, const T *r, T *z, T *x, const T *d, T 
     case 2: launch_vanka_u_tile<T, 8, 8, 128>(a, L, st); break;
     case 3: launch_vanka_u_tile<T, 8, 4, 128>(a, L, st); break;
     case 4: launch_vanka_u_tile<T, 4, 4, 64>(a, L, st); break;
+    case 5: launch_vanka_u_tile<T, 32, 8, 256, true>(a, L, st); break;   // one thread per patch solve
+    case 6: launch_vanka_u_tile<T, 16, 8, 128, true>(a, L, st); break;
+    case 7: launch_vanka_u_tile<T, 8, 8, 64, true>(a, L, st); break;
     default:
       if (ctas(32, 8) >= want) launch_vanka_u_tile<T, 32, 8, 256>(a, L, st);
       else if (ctas(16, 8) >= want) launch_vanka_u_tile<T, 16, 8, 256>(a, L, st);
