@@ -666,7 +666,7 @@ def bsr_exact_workload(n, lams=(1.0, 1e4, 1e6), Ks=(1.0, 1e-6)):
             rows.append(row)
             del s
     return {"workload": f"exact vs inexact BSR V(1,1), {n}x{n}, the sweep's BSR points (lambda x K), "
-                        "FGMRES(50) to 1e-8; exact: Jacobi-CG on the fixed-stress S to 1e-11",
+                        "FGMRES(50) to 1e-8; exact: CG on the fixed-stress S to 1e-11, multigrid-preconditioned",
             "free_dofs": bmg.free_dofs(n), "solves": rows}
 
 

@@ -74,7 +74,8 @@ extern "C" {
 #define BMG_VANKA 0           /* additive Vanka, 20-DoF vertex patches (Sec. 3.2.1)     */
 #define BMG_BSR 1             /* inexact Braess-Sarazin (Sec. 3.2.2, App. D)            */
 #define BMG_BSR_EXACT 2       /* exact Braess-Sarazin: Eq. bsr_p solved with the fixed-stress
-                                 S (Jacobi-preconditioned CG to 1e-11 relative, FP64 only,
+                                 S (CG to 1e-11 relative, preconditioned by a multigrid
+                                 V-cycle on the coarser levels' S, FP64 only,
                                  V-cycles kernel by kernel; BMG_ERR_NOCONV if CG stalls)   */
 #define BMG_FP64 0
 #define BMG_FP32 1

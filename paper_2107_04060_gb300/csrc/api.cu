@@ -92,7 +92,7 @@ static void free_level(Level &L) {
   cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
   cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
   cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2); cudaFree(L.wz);
-  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.cg); cudaFree(L.cg_flag);
+  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.cg); cudaFree(L.cg_flag); cudaFree(L.smg);
   L = Level();
 }
 
@@ -646,7 +646,8 @@ static int smooth(bmg_hierarchy *h, const Level &L, const T *r, T *x, cudaStream
   if (h->opts.smoother == BMG_VANKA) return launch_vanka_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);
   if (h->opts.smoother == BMG_BSR_EXACT) {
     if constexpr (std::is_same<T, double>::value)
-      return launch_bsr_exact_sweep(L, r, x, h->opts.omega, st, assign, &h->schur_iters_max);
+      return launch_bsr_exact_sweep(h->levels.data(), (int)h->levels.size() - 1, (int)(&L - h->levels.data()), r,
+                                    x, h->opts.omega, st, assign, &h->schur_iters_max);
     return arg_error("exact BSR runs in FP64 only");
   }
   return launch_bsr_sweep<T>(L, r, x, (T)h->opts.omega, st, assign);

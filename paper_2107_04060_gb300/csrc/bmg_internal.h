@@ -153,7 +153,8 @@ struct Level {
   double s_c = 0.0;                    // (1/M + alpha^2/(lambda + mu)) |T|
   double *cg = nullptr;                // r, z, q, p[2] (5 x 2 blk), then the block partials
   int cg_grid = 0;                     // CTAs of the CG kernels (partials per reduction)
-  int *cg_flag = nullptr;              // device [done, iterations, rr0 valid]
+  int *cg_flag = nullptr;              // device [done, iterations]
+  double *smg = nullptr;               // multigrid preconditioner of S: b, xa, xb, r, e (5 x 2 blk)
   // coarsest level: dense inverse on the free DoFs
   int nfree = 0;
   int *free_idx = nullptr;     // [nfree] vector positions of the free DoFs
@@ -350,8 +351,8 @@ template <typename T>
 int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st);
 int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st);
 int bsr_exact_setup(Level &L, cudaStream_t st);
-int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double omega, cudaStream_t st,
-                           bool assign, int *iters_max);
+int launch_bsr_exact_sweep(const Level *levels, int nsmooth, int l, const double *r, double *x, double omega,
+                           cudaStream_t st, bool assign, int *iters_max);
 template <typename T>
 int launch_bsr_sweep(const Level &L, const T *r, T *x, T omega, cudaStream_t st, bool assign);
 // vector kernels

@@ -424,8 +424,10 @@ template int launch_bsr_sweep<float>(const Level &, const float *, float *, floa
 
 // ---- exact BSR (Sec. 3.2.2: Eq. bsr_p with the fixed-stress S solved, not relaxed) -------
 // S = c I + (tau B_w) (tau D_w)^{-1} (tau B_w)^T on the P0 space, c = (1/M + alpha^2/(lambda +
-// mu)) |T|, is symmetric positive definite; the pressure step runs Jacobi-preconditioned
-// conjugate gradients on it to a relative residual of kCgRtol.  The P0 space is the two
+// mu)) |T|, is symmetric positive definite; the pressure step runs preconditioned conjugate
+// gradients on it to a relative residual of kCgRtol: with a multigrid V-cycle on the S of the
+// coarser levels (smg_vcycle below) where the hierarchy has them, with Jacobi on its last
+// smoothing level.  The P0 space is the two
 // triangle blocks (L, U) of blk slots each; cell (i, j) sits at j * pitch + i in both, and the
 // slots outside the n x n cells stay zero in every CG vector.  Per triangle the product is
 //   (S y)_T = c y_T + sum_{edges e of T} (tau B_w)_{T,e} (tau D_w)_e^{-1} sum_{T' on e} (tau B_w)_{T',e} y_T'
@@ -437,12 +439,13 @@ template int launch_bsr_sweep<float>(const Level &, const float *, float *, floa
 //                 in the same order, so all see the same scalars); stop test; beta; the new
 //                 direction p_k = z + beta p_{k-1} on the cell and its four neighbours (so no
 //                 CTA waits for another); q = S p_k; partials of p_k . q
-//   update(k):    alpha = rz_k / (p_k . q); x += alpha p_k; r -= alpha q; z = D^{-1} r;
-//                 partials of r . z and r . r
+//   update(k):    alpha = rz_k / (p_k . q); x += alpha p_k; r -= alpha q; with Jacobi:
+//                 z = D^{-1} r and the partials of r . z and r . r; with the multigrid
+//                 preconditioner the V-cycle's kernels form z and cg_dots_kernel the partials
 // Partials, rz and the direction alternate between two slots by iteration parity, so a kernel
 // never overwrites what a CTA of the same launch still reads.  A device flag ends the
 // iteration: the kernels after the stop return at once, and the host reads the flag every
-// kCgCheck iterations.
+// kCgCheck iterations (every 4 with the multigrid preconditioner).
 constexpr int kCgThreads = 256;
 constexpr double kCgRtol = 1e-11;
 constexpr int kCgMaxIt = 20000;
@@ -462,7 +465,32 @@ struct CgArgs {
   int *flag;                // [0] 0 running, 1 converged, 2 non-finite; [1] iterations
   int k;
   double tol2;
+  int mg;                   // 1: z = M r by the multigrid preconditioner (separate kernels)
 };
+
+// (S y) at the two triangles of cell (i, j) of an n x n level; val(e) gives y at slot e of the
+// two-block P0 vector (e in [0, 2 blk)).
+template <typename F>
+__device__ __forceinline__ void s_product(const Grid &g, double c, const double (&dw)[2][3], const double *dinv,
+                                          int i, int j, F &&val, double &yL, double &yU, double &qL,
+                                          double &qU) {
+  const int n = g.n, P = g.pitch;
+  const size_t blk = g.blk, o = (size_t)j * P + i;
+  yL = val(o);
+  yU = val(blk + o);
+  const double yUw = i > 0 ? val(blk + o - 1) : 0.0;        // U(i-1, j)
+  const double yUs = j > 0 ? val(blk + o - P) : 0.0;        // U(i, j-1)
+  const double yLe = i + 1 < n ? val(o + 1) : 0.0;          // L(i+1, j)
+  const double yLn = j + 1 < n ? val(o + P) : 0.0;          // L(i, j+1)
+  const double L0 = dw[0][0], L1 = dw[0][1], L2 = dw[0][2];
+  const double U0 = dw[1][0], U1 = dw[1][1], U2 = dw[1][2];
+  const double id = dinv[2 * blk + o];                      // d(i, j)
+  const double ivL = dinv[1 * blk + o], ivU = dinv[1 * blk + o + 1];   // v(i, j), v(i+1, j)
+  const double ihL = dinv[0 * blk + o], ihU = dinv[0 * blk + o + P];   // h(i, j), h(i, j+1)
+  const double fd = id * fma(L0, yL, U0 * yU);
+  qL = c * yL + L0 * fd + L1 * ivL * fma(L1, yL, U1 * yUw) + L2 * ihL * fma(L2, yL, U2 * yUs);
+  qU = c * yU + U0 * fd + U1 * ivU * fma(U1, yU, L1 * yLe) + U2 * ihU * fma(U2, yU, L2 * yLn);
+}
 
 __device__ __forceinline__ double cg_block_sum(double v, double *sh) {
 #pragma unroll
@@ -502,9 +530,10 @@ __global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const __grid_consta
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const size_t e = t * blk + o;
+      a.x[e] = 0.0;
+      if (a.mg) continue;
       const double r = a.r[e], z = a.minv[e] * r;
       a.z[e] = z;
-      a.x[e] = 0.0;
       rz = fma(r, z, rz);
       rr = fma(r, r, rr);
     }
@@ -545,24 +574,12 @@ __global__ void __launch_bounds__(kCgThreads) cg_dir_apply_kernel(const __grid_c
   double *pn = a.p[par];
   // p_k at slot e (k = 0: z alone, the other slot is not read)
   auto pk = [&](size_t e) { return k == 0 ? z[e] : fma(beta, po[e], z[e]); };
-  const double c = a.c;
-  const double L0 = a.dw[0][0], L1 = a.dw[0][1], L2 = a.dw[0][2];
-  const double U0 = a.dw[1][0], U1 = a.dw[1][1], U2 = a.dw[1][2];
   double pq = 0.0;
   for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += G * kCgThreads) {
     const int i = cc % n, j = cc / n;
     const size_t o = (size_t)j * P + i;
-    const double pL = pk(o), pU = pk(blk + o);
-    const double pUw = i > 0 ? pk(blk + o - 1) : 0.0;        // U(i-1, j)
-    const double pUs = j > 0 ? pk(blk + o - P) : 0.0;        // U(i, j-1)
-    const double pLe = i + 1 < n ? pk(o + 1) : 0.0;          // L(i+1, j)
-    const double pLn = j + 1 < n ? pk(o + P) : 0.0;          // L(i, j+1)
-    const double id = a.dinv[2 * blk + o];                   // d(i, j)
-    const double ivL = a.dinv[1 * blk + o], ivU = a.dinv[1 * blk + o + 1];   // v(i, j), v(i+1, j)
-    const double ihL = a.dinv[0 * blk + o], ihU = a.dinv[0 * blk + o + P];   // h(i, j), h(i, j+1)
-    const double fd = id * fma(L0, pL, U0 * pU);
-    const double qL = c * pL + L0 * fd + L1 * ivL * fma(L1, pL, U1 * pUw) + L2 * ihL * fma(L2, pL, U2 * pUs);
-    const double qU = c * pU + U0 * fd + U1 * ivU * fma(U1, pU, L1 * pLe) + U2 * ihU * fma(U2, pU, L2 * pLn);
+    double pL, pU, qL, qU;
+    s_product(a.g, a.c, a.dw, a.dinv, i, j, pk, pL, pU, qL, qU);
     pn[o] = pL;
     pn[blk + o] = pU;
     a.q[o] = qL;
@@ -591,19 +608,197 @@ __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(const __grid_cons
       const size_t e = t * blk + o;
       a.x[e] = fma(alpha, p[e], a.x[e]);
       const double r = fma(-alpha, a.q[e], a.r[e]);
-      const double z = a.minv[e] * r;
       a.r[e] = r;
+      if (a.mg) continue;
+      const double z = a.minv[e] * r;
       a.z[e] = z;
       rz = fma(r, z, rz);
       rr = fma(r, r, rr);
     }
   }
+  if (a.mg) return;                          // the partials come from cg_dots_kernel
   rz = cg_block_sum(rz, sh);
   rr = cg_block_sum(rr, sh);
   if (threadIdx.x == 0) {
     a.part[(0 + (par ^ 1)) * G + blockIdx.x] = rz;
     a.part[(2 + (par ^ 1)) * G + blockIdx.x] = rr;
   }
+}
+
+// Multigrid preconditioner: the partials of r . z and r . r for the next iteration (slot
+// (k + 1) & 1; k = -1 before the first one).
+__global__ void __launch_bounds__(kCgThreads) cg_dots_kernel(const __grid_constant__ CgArgs a) {
+  __shared__ double sh[kCgThreads / 32];
+  if (cg_stopped(a.flag)) return;
+  const int n = a.g.n, P = a.g.pitch, G = gridDim.x, slot = (a.k + 1) & 1;
+  const size_t blk = a.g.blk;
+  double rz = 0.0, rr = 0.0;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += G * kCgThreads) {
+    const size_t o = (size_t)(cc / n) * P + cc % n;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const double r = a.r[t * blk + o];
+      rz = fma(r, a.z[t * blk + o], rz);
+      rr = fma(r, r, rr);
+    }
+  }
+  rz = cg_block_sum(rz, sh);
+  rr = cg_block_sum(rr, sh);
+  if (threadIdx.x == 0) {
+    a.part[(0 + slot) * G + blockIdx.x] = rz;
+    a.part[(2 + slot) * G + blockIdx.x] = rr;
+  }
+}
+
+// ---- multigrid V-cycle for S (the CG's preconditioner) ----------------------------------
+// Levels of the hierarchy below the one being relaxed, each with its own rediscretised S
+// (its c, (tau B_w) and (tau D_w)^{-1}).  For uniform K the Galerkin product P^T S P keeps
+// c |T| and sums the two fine edges of every coarse edge (twice the rediscretised flux
+// part); the rediscretised operator's smaller coarse flux over-corrects, which the
+// piecewise-constant prolongation needs (measured at 512^2, K = 1: 115 CG iterations per
+// pressure step against 153 with the Galerkin-scaled operators).  Weighted Jacobi smoothing (kSmgOmega D^{-1}, two
+// steps before and after the coarse correction, eight from zero on the last level), P0
+// restriction by summing the four child triangles and prolongation by injection (R = P^T).
+// With the same smoothing before and after and R = P^T the cycle is a symmetric positive
+// definite operator, as conjugate gradients needs.  Children of coarse cell (I, J): coarse L
+// holds L and U of fine (2I, 2J) and L of (2I+1, 2J), (2I, 2J+1); coarse U holds L and U of
+// (2I+1, 2J+1) and U of (2I+1, 2J), (2I, 2J+1).  The kernels return at once once the CG has
+// stopped.
+constexpr double kSmgOmega = 2.0 / 3.0;
+constexpr int kSmgBottom = 8;
+constexpr int kSmgVecs = 5;                  // b, xa, xb, r, e (2 blk each)
+
+struct SOp {
+  Grid g;
+  double c;
+  double dw[2][3];
+  const double *dinv, *minv;  // minv: 1 / diag(S)
+  const int *stop;
+};
+
+// xout = xin + w D^{-1} (b - S xin)   (xin == nullptr: from zero, xout = w D^{-1} b)
+__global__ void __launch_bounds__(kCgThreads) s_jacobi_kernel(const __grid_constant__ SOp o, const double *b,
+                                                              const double *xin, double *xout, double w) {
+  if (*(volatile const int *)o.stop) return;
+  const int n = o.g.n, P = o.g.pitch;
+  const size_t blk = o.g.blk;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += gridDim.x * kCgThreads) {
+    const int i = cc % n, j = cc / n;
+    const size_t e = (size_t)j * P + i;
+    if (!xin) {
+      xout[e] = w * o.minv[e] * b[e];
+      xout[blk + e] = w * o.minv[blk + e] * b[blk + e];
+      continue;
+    }
+    double yL, yU, qL, qU;
+    s_product(o.g, o.c, o.dw, o.dinv, i, j, [&](size_t k) { return xin[k]; }, yL, yU, qL, qU);
+    xout[e] = fma(w * o.minv[e], b[e] - qL, yL);
+    xout[blk + e] = fma(w * o.minv[blk + e], b[blk + e] - qU, yU);
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) s_residual_kernel(const __grid_constant__ SOp o, const double *b,
+                                                                const double *x, double *r) {
+  if (*(volatile const int *)o.stop) return;
+  const int n = o.g.n, P = o.g.pitch;
+  const size_t blk = o.g.blk;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += gridDim.x * kCgThreads) {
+    const int i = cc % n, j = cc / n;
+    const size_t e = (size_t)j * P + i;
+    double yL, yU, qL, qU;
+    s_product(o.g, o.c, o.dw, o.dinv, i, j, [&](size_t k) { return x[k]; }, yL, yU, qL, qU);
+    r[e] = b[e] - qL;
+    r[blk + e] = b[blk + e] - qU;
+  }
+}
+
+// b_c = P^T r_f (one thread per coarse cell)
+__global__ void __launch_bounds__(kCgThreads) s_restrict_kernel(Grid gf, Grid gc, const double *rf, double *bc,
+                                                                const int *stop) {
+  if (*(volatile const int *)stop) return;
+  const int nc = gc.n;
+  const size_t bf = gf.blk, bcb = gc.blk;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < nc * nc; cc += gridDim.x * kCgThreads) {
+    const int I = cc % nc, J = cc / nc;
+    const size_t f00 = (size_t)(2 * J) * gf.pitch + 2 * I, f10 = f00 + 1, f01 = f00 + gf.pitch, f11 = f01 + 1;
+    const size_t c = (size_t)J * gc.pitch + I;
+    bc[c] = (rf[f00] + rf[bf + f00]) + (rf[f10] + rf[f01]);
+    bc[bcb + c] = (rf[f11] + rf[bf + f11]) + (rf[bf + f10] + rf[bf + f01]);
+  }
+}
+
+// xout = xin + P e_c (one thread per fine cell)
+__global__ void __launch_bounds__(kCgThreads) s_prolong_kernel(Grid gf, Grid gc, const double *xin,
+                                                               const double *ec, double *xout, const int *stop) {
+  if (*(volatile const int *)stop) return;
+  const int n = gf.n;
+  const size_t bf = gf.blk, bcb = gc.blk;
+  for (int cc = blockIdx.x * kCgThreads + threadIdx.x; cc < n * n; cc += gridDim.x * kCgThreads) {
+    const int i = cc % n, j = cc / n;
+    const size_t f = (size_t)j * gf.pitch + i, c = (size_t)(j / 2) * gc.pitch + i / 2;
+    const int a = i & 1, b = j & 1;
+    const double eL = ec[c], eU = ec[bcb + c];
+    xout[f] = xin[f] + ((a & b) ? eU : eL);              // fine L: coarse U only in the (1, 1) child
+    xout[bf + f] = xin[bf + f] + ((a | b) ? eU : eL);    // fine U: coarse L only in the (0, 0) child
+  }
+}
+
+static SOp sop_of(const Level &L, const int *stop) {
+  SOp o;
+  o.g = L.g;
+  o.c = L.s_c;
+  for (int t = 0; t < 2; ++t)
+    for (int k = 0; k < 3; ++k) o.dw[t][k] = L.c64.dw[t][k];
+  o.dinv = L.dinv64;
+  o.minv = L.sinv64;
+  o.stop = stop;
+  return o;
+}
+
+static int smg_grid(const Level &L) {
+  const long long cells = (long long)L.n * L.n;
+  return (int)std::min<long long>((cells + kCgThreads - 1) / kCgThreads, 4 * 152);
+}
+
+// out = M_l b on level l of `levels` (levels l .. nsmooth - 1 carry S); b and out are 2-blk
+// vectors of level l, out distinct from the level's work vectors.
+static int smg_vcycle(const Level *levels, int nsmooth, int l, const double *b, double *out, const int *stop,
+                      cudaStream_t st) {
+  const Level &L = levels[l];
+  const size_t v = 2 * L.g.blk;
+  double *xa = L.smg + 1 * v, *xb = L.smg + 2 * v, *r = L.smg + 3 * v;
+  const SOp o = sop_of(L, stop);
+  const dim3 grid(smg_grid(L)), block(kCgThreads);
+  if (l + 1 >= nsmooth) {                   // last level: Jacobi steps from zero
+    const double *xin = nullptr;
+    for (int s = 0; s < kSmgBottom; ++s) {
+      double *xo = s + 1 == kSmgBottom ? out : (s & 1 ? xb : xa);
+      s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, xin, xo, kSmgOmega);
+      BMG_CHECK_LAUNCH("s_jacobi_kernel");
+      xin = xo;
+    }
+    return BMG_OK;
+  }
+  const Level &C = levels[l + 1];
+  const size_t vc = 2 * C.g.blk;
+  double *bc = C.smg, *ec = C.smg + 4 * vc;
+  s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, nullptr, xa, kSmgOmega);
+  BMG_CHECK_LAUNCH("s_jacobi_kernel");
+  s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, xa, xb, kSmgOmega);
+  BMG_CHECK_LAUNCH("s_jacobi_kernel");
+  s_residual_kernel<<<grid, block, 0, st>>>(o, b, xb, r);
+  BMG_CHECK_LAUNCH("s_residual_kernel");
+  s_restrict_kernel<<<dim3(smg_grid(C)), block, 0, st>>>(L.g, C.g, r, bc, stop);
+  BMG_CHECK_LAUNCH("s_restrict_kernel");
+  int rc = smg_vcycle(levels, nsmooth, l + 1, bc, ec, stop, st);
+  if (rc) return rc;
+  s_prolong_kernel<<<grid, block, 0, st>>>(L.g, C.g, xb, ec, xa, stop);
+  BMG_CHECK_LAUNCH("s_prolong_kernel");
+  s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, xa, xb, kSmgOmega);
+  BMG_CHECK_LAUNCH("s_jacobi_kernel");
+  s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, xb, out, kSmgOmega);
+  BMG_CHECK_LAUNCH("s_jacobi_kernel");
+  return BMG_OK;
 }
 
 // Work space of the exact pressure step and 1 / diag(S) (sinv with omega_J = 1).
@@ -616,13 +811,17 @@ int bsr_exact_setup(Level &L, cudaStream_t st) {
   BMG_CUDA(cudaMemsetAsync(L.cg, 0, sizeof(double) * len, st));
   BMG_CUDA(cudaMalloc(&L.cg_flag, sizeof(int) * 2));
   BMG_CUDA(cudaMemsetAsync(L.cg_flag, 0, sizeof(int) * 2, st));
+  BMG_CUDA(cudaMalloc(&L.smg, sizeof(double) * kSmgVecs * 2 * blk));
+  BMG_CUDA(cudaMemsetAsync(L.smg, 0, sizeof(double) * kSmgVecs * 2 * blk, st));
   return BMG_OK;
 }
 
 // x <- x + omega (dy, dp) with dp = S^{-1}(B z - r_p) from conjugate gradients.  Runs kernel by
 // kernel with host reads of the stop flag (not capturable into a graph).
-int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double omega, cudaStream_t st,
-                           bool assign, int *iters_max) {
+int launch_bsr_exact_sweep(const Level *levels, int nsmooth, int l, const double *r, double *x, double omega,
+                           cudaStream_t st, bool assign, int *iters_max) {
+  const Level &L = levels[l];
+  const bool mg = l + 1 < nsmooth;         // a coarser level with S below: multigrid preconditioner
   if (capturing(st)) {
     set_error("exact BSR reads its stop flag on the host and cannot be captured into a graph");
     return BMG_ERR_ARG;
@@ -650,6 +849,7 @@ int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double om
   c.flag = L.cg_flag;
   c.k = 0;
   c.tol2 = kCgRtol * kCgRtol;
+  c.mg = mg ? 1 : 0;
   BMG_PROF_BEGIN(BMG_PROF_SCHUR, L.n, st);
   {
     DpArgs<double> a;
@@ -668,6 +868,17 @@ int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double om
   const dim3 grid(L.cg_grid), block(kCgThreads);
   cg_init_kernel<<<grid, block, 0, st>>>(c);
   BMG_CHECK_LAUNCH("cg_init_kernel");
+  // z = M r and the partials of r . z, r . r for iteration k + 1
+  auto precondition = [&](int k) -> int {
+    int rc2 = smg_vcycle(levels, nsmooth, l, c.r, c.z, L.cg_flag, st);
+    if (rc2) return rc2;
+    c.k = k;
+    cg_dots_kernel<<<grid, block, 0, st>>>(c);
+    BMG_CHECK_LAUNCH("cg_dots_kernel");
+    return BMG_OK;
+  };
+  if (mg && (rc = precondition(-1))) return rc;
+  const int check = mg ? 4 : kCgCheck;
   int hflag[2] = {0, 0};
   for (int k = 0; k < kCgMaxIt; ++k) {
     c.k = k;
@@ -675,7 +886,8 @@ int launch_bsr_exact_sweep(const Level &L, const double *r, double *x, double om
     BMG_CHECK_LAUNCH("cg_dir_apply_kernel");
     cg_update_kernel<<<grid, block, 0, st>>>(c);
     BMG_CHECK_LAUNCH("cg_update_kernel");
-    if ((k + 1) % kCgCheck == 0 || k + 1 == kCgMaxIt) {
+    if (mg && (rc = precondition(k))) return rc;
+    if ((k + 1) % check == 0 || k + 1 == kCgMaxIt) {
       BMG_CUDA(cudaMemcpyAsync(hflag, L.cg_flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
       BMG_CUDA(cudaStreamSynchronize(st));
       if (hflag[0]) break;

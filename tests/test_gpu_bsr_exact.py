@@ -1,7 +1,8 @@
 """Exact Braess-Sarazin relaxation on the GPU (smoother "bsr_exact": Sec. 3.2.2, Eq. bsr_p with
 the fixed-stress S solved, not relaxed) against the oracle's exact BSR (sparse LU of S).
 
-The GPU solves S dp = B z - r_p by Jacobi-preconditioned CG to a relative residual of 1e-11,
+The GPU solves S dp = B z - r_p by preconditioned CG (a multigrid V-cycle on the coarser
+levels' S, Jacobi on the last smoothing level) to a relative residual of 1e-11,
 so dp carries a relative error up to kappa(S) 1e-11; the V-cycle tolerance is 1e-9 (the FP64
 V-cycle parity bound) plus 10 kappa(S) 1e-11 with kappa(S) of the finest level computed here
 from the oracle's S (coarser levels have smaller kappa).
