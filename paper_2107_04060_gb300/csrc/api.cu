@@ -373,11 +373,15 @@ static int setup_patches(bmg_hierarchy *h, Level &L, int psize, double p_shift,
 // value is formed by the same arithmetic whichever tile holds it.
 template <typename F>
 static int time_min(F &&launch, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float *ms) {
+  // the best of three timings of three back-to-back launches (single launches of ~100 us
+  // differ by less than their timing noise)
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     BMG_CUDA(cudaEventRecord(e0, st));
-    int rc = launch();
-    if (rc) return rc;
+    for (int k = 0; k < 3; ++k) {
+      int rc = launch();
+      if (rc) return rc;
+    }
     BMG_CUDA(cudaEventRecord(e1, st));
     BMG_CUDA(cudaEventSynchronize(e1));
     float t = 0.f;
