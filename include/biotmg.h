@@ -379,7 +379,9 @@ int bmg_hierarchy_levels(const bmg_hierarchy *h);
  * 2 = 8 x 8, 3 = 8 x 4, 4 = 4 x 4 output positions (Vanka: patches),
  * 5 = FP32 operator, 32 x 8 with its input staged in shared memory by TMA bulk tensor
  * copies (FP64: the 32 x 8 tile), 6 = 32 x 8 and 7 = 16 x 8 operator tiles with registers
- * capped for 4 and 8 CTAs per SM; Vanka and displacement Vanka 5 = 32 x 8, 6 = 16 x 8,
+ * capped for 4 and 8 CTAs per SM, 8 = 32 x 8 and 9 = 16 x 8 FP64 operator tiles that load
+ * the residual's b before the element products (the FP32 operator does so in every tile);
+ * Vanka and displacement Vanka 5 = 32 x 8, 6 = 16 x 8,
  * 7 = 8 x 8 patches solved one patch per thread
  * (each packed inverse entry loaded once) instead of (row, patch) tasks.  -1: not tuned or
  * no such level.  The choice does not change any result.  Setting

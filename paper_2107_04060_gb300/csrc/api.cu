@@ -425,7 +425,7 @@ static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1
   if (force && *force) {
     L.tile_apply = std::atoi(force);
   } else {
-    rc = pick_tile(&L.tile_apply, 0, 7,
+    rc = pick_tile(&L.tile_apply, 0, sizeof(T) == 8 ? 9 : 7,
                    [&] { return launch_apply<T>(L, z, r, t, true, 1, 0, st); }, e0, e1, st);
     if (rc) return rc;
   }
@@ -459,7 +459,7 @@ static int tune_hierarchy(bmg_hierarchy *h, cudaStream_t st) {
       rc = cuda_fail(cudaErrorMemoryAllocation, "tuning vectors");
     } else {
       cudaMemsetAsync(a, 0, sizeof(double) * vl, st);
-      rc = pick_tile(&F.tile_apply, 0, 7, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
+      rc = pick_tile(&F.tile_apply, 0, 9, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
                      e0, e1, st);
     }
     cudaStreamSynchronize(st);

@@ -229,7 +229,10 @@ __host__ __device__ constexpr int round32(int v) { return (v + 31) / 32 * 32; }
 // Tile of kTX x kTY output positions per CTA (template: large tiles on large grids, small
 // tiles on the coarse levels so that their work spreads over many SMs).  sy: shared scratch
 // of kCellSlots values per cell of the tile and of its one-cell halo on the low side.
-template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, typename Src>
+// PF: the residual form loads the thread's b values before the element products, so their
+// latency overlaps phase 1 instead of following the barrier (always in FP32; an FP64 tuning
+// candidate, since it holds 20 more registers through phase 1).
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, typename Src, bool PF = (sizeof(T) == 4)>
 __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src, T (*sy)[kCellSlots], int bx,
                                            int by, size_t boff) {
   constexpr int kEX = kTX + 1;
@@ -248,6 +251,16 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
   const int i0 = bx * kTX, j0 = by * kTY;
   const int tid = threadIdx.x;
   auto S = [&](int ci, int cj) -> T * { return sy[(cj - j0 + 1) * kEX + (ci - i0 + 1)]; };
+  constexpr bool kPrefetchB = PF;
+  T bpre[NBLK];
+  if constexpr (kPrefetchB) {
+    const int ip = i0 + tid % kTX, jp = j0 + tid / kTX;
+    const bool ok = a.residual && tid < kOwn && jp <= n && ip <= n;
+    const T *bb = a.b + boff;
+    const size_t op = (size_t)jp * P + ip;
+#pragma unroll
+    for (int k = 0; k < NBLK; ++k) bpre[k] = ok ? bb[k * blk + op] : T(0);
+  }
 
   // phase 1: one task per cell of the tile (both triangles), then the halo cells with only
   // the rows the tile gathers
@@ -293,22 +306,43 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs<T> &a, const Src &src
 #pragma unroll
   for (int k = 0; k < NBLK; ++k) {
     T out = 0;
-    if (m[k]) out = a.residual ? b[k * blk + o] - v[k] : v[k];
+    if constexpr (kPrefetchB) {
+      if (m[k]) out = a.residual ? bpre[k] - v[k] : v[k];
+    } else {
+      if (m[k]) out = a.residual ? b[k * blk + o] - v[k] : v[k];
+    }
     y[k * blk + o] = out;
   }
 }
 
-// MINB > 1 caps the registers so that MINB CTAs fit on an SM (more warps to hide the loads
-// and the barrier, at the price of a few spilled values): tuning candidates.
-template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, int MINB = 1>
-__global__ void __launch_bounds__(NT, MINB) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, bool PF>
+__device__ __forceinline__ void apply_global(const ApplyArgs<T> &a) {
   pdl_enter();
   BMG_GATE(a.gate);
   extern __shared__ unsigned char smem_raw[];
   const size_t boff = (size_t)blockIdx.z * a.bstride;
   const GlobalSrc<T> src{a.x + boff, a.kinv, a.wm, a.g.blk, a.g.pitch};
-  apply_tile<T, WM, kTX, kTY, NT, DENSE>(a, src, reinterpret_cast<T(*)[kCellSlots]>(smem_raw), blockIdx.x,
-                                        blockIdx.y, boff);
+  apply_tile<T, WM, kTX, kTY, NT, DENSE, GlobalSrc<T>, PF>(a, src, reinterpret_cast<T(*)[kCellSlots]>(smem_raw),
+                                                           blockIdx.x, blockIdx.y, boff);
+}
+
+// MINB > 1 caps the registers so that MINB CTAs fit on an SM (more warps to hide the loads
+// and the barrier, at the price of a few spilled values): tuning candidates.  MINB = 1 keeps
+// the plain bound (an explicit minimum of one CTA lets the compiler take more registers).
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, bool PF>
+__global__ void __launch_bounds__(NT) apply_kernel(const __grid_constant__ ApplyArgs<T> a) {
+  apply_global<T, WM, kTX, kTY, NT, DENSE, PF>(a);
+}
+
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, int MINB, bool PF>
+__global__ void __launch_bounds__(NT, MINB) apply_kernel_capped(const __grid_constant__ ApplyArgs<T> a) {
+  apply_global<T, WM, kTX, kTY, NT, DENSE, PF>(a);
+}
+
+template <typename T, int WM, int kTX, int kTY, int NT, bool DENSE, int MINB, bool PF>
+constexpr auto apply_kernel_ptr() {
+  if constexpr (MINB > 1) return &apply_kernel_capped<T, WM, kTX, kTY, NT, DENSE, MINB, PF>;
+  else return &apply_kernel<T, WM, kTX, kTY, NT, DENSE, PF>;
 }
 
 // Batched form: several instances of one grid size in one launch, blockIdx.z selecting the
@@ -488,7 +522,7 @@ void free_apply_tma(Level &L) {
   L.tma = nullptr;
 }
 
-template <typename T, int WM, int TX, int TY, int NT, bool DENSE, int MINB = 1>
+template <typename T, int WM, int TX, int TY, int NT, bool DENSE, int MINB = 1, bool PF = (sizeof(T) == 4)>
 static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, cudaStream_t st) {
   dim3 block(NT);
   dim3 grid((L.g.pitch + TX - 1) / TX, (L.n + 1 + TY - 1) / TY, batch);
@@ -496,12 +530,12 @@ static int launch_apply_tile(const ApplyArgs<T> &a, const Level &L, int batch, c
   if (smem > 48 * 1024) {
     static bool attr = false;
     if (!attr) {
-      BMG_CUDA(cudaFuncSetAttribute(apply_kernel<T, WM, TX, TY, NT, DENSE, MINB>,
+      BMG_CUDA(cudaFuncSetAttribute(apply_kernel_ptr<T, WM, TX, TY, NT, DENSE, MINB, PF>(),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr = true;
     }
   }
-  BMG_CUDA(launch_pdl(apply_kernel<T, WM, TX, TY, NT, DENSE, MINB>, dim3(grid), dim3(block), smem, st, a));
+  BMG_CUDA(launch_pdl(apply_kernel_ptr<T, WM, TX, TY, NT, DENSE, MINB, PF>(), dim3(grid), dim3(block), smem, st, a));
   return BMG_OK;
 }
 
@@ -527,6 +561,12 @@ static int launch_apply_wm(const ApplyArgs<T> &a, const Level &L, int batch, cud
       return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
     case 6: return launch_apply_tile<T, WM, 32, 8, 256, D, 4>(a, L, batch, st);   // 4 CTAs / SM
     case 7: return launch_apply_tile<T, WM, 16, 8, 128, D, 8>(a, L, batch, st);   // 8 CTAs / SM
+    case 8:                         // FP64 with b prefetched (FP32 prefetches in every tile)
+      if constexpr (sizeof(T) == 8) return launch_apply_tile<T, WM, 32, 8, 256, D, 1, true>(a, L, batch, st);
+      return launch_apply_tile<T, WM, 32, 8, 256, D>(a, L, batch, st);
+    case 9:
+      if constexpr (sizeof(T) == 8) return launch_apply_tile<T, WM, 16, 8, 128, D, 1, true>(a, L, batch, st);
+      return launch_apply_tile<T, WM, 16, 8, 128, D>(a, L, batch, st);
     default: break;
   }
   // the largest tile that still gives every SM about two CTAs

@@ -73,8 +73,9 @@ CASES = [("vanka", 0.8, "const"), ("vanka", 0.7, "lognormal"), ("bsr", 0.7, "con
 def test_vcycle_parity_every_tile_n128(bmg, smoother, omega, kind):
     """n = 128 (five levels down to 8): every tile candidate of the operator and of the
     smoother, constant coefficients (symmetry-adapted interior Vanka solve) and lognormal K
-    (per-patch inverses); the register-capped operator tiles 6 and 7, and the smoothers'
-    one-thread-per-patch candidates 5-7 with the 32 x 8 operator tile."""
+    (per-patch inverses); the register-capped operator tiles 6 and 7, the operator tiles 8
+    and 9 that load b first, and the smoothers' one-thread-per-patch candidates 5-7 with the
+    32 x 8 operator tile."""
     import torch
     n = 128
     p = dict(lam=1.0, mu=1.0, tau=1.0, alpha=1.0, inv_M=1.0) if kind == "const" else \
@@ -92,7 +93,7 @@ def test_vcycle_parity_every_tile_n128(bmg, smoother, omega, kind):
     f = synthetic.rhs(n, 5)
     zo = H.vcycle(H.levels[0].mesh.pack(f))
     r = dev(bmg, n, f)
-    combos = [(t, t) for t in range(5)] + [(0, 6), (1, 7)]        # (smoother, operator)
+    combos = [(t, t) for t in range(5)] + [(0, 6), (1, 7), (0, 8), (1, 9)]   # (smoother, operator)
     combos += [(5, 0), (6, 0), (7, 0)]                             # one thread per patch solve
     for tile, at in combos:
         h = setup_forced(bmg, s, smoother, omega, tile, apply_tile=at)
