@@ -92,7 +92,7 @@ static void free_level(Level &L) {
   cudaFree(L.dinv64); cudaFree(L.dinv32); cudaFree(L.sinv64); cudaFree(L.sinv32);
   cudaFree(L.free_idx); cudaFree(L.cinv64); cudaFree(L.cinv32);
   cudaFree(L.rhs); cudaFree(L.z); cudaFree(L.t); cudaFree(L.t2); cudaFree(L.wz);
-  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.cg); cudaFree(L.cg_flag); cudaFree(L.smg);
+  cudaFree(L.bz); cudaFree(L.bd); cudaFree(L.cg); cudaFree(L.cg_flag); cudaFree(L.smg); cudaFree(L.sdense);
   L = Level();
 }
 
@@ -593,6 +593,11 @@ extern "C" int bmg_setup_hierarchy(const bmg_system *s, const bmg_mg_opts *o, vo
   }
   int rc = coarse_setup(h->levels.back(), h->d_flag, st);
   if (rc) return fail(rc);
+  // exact BSR: the last smoothing level's S factored once (the bottom of the multigrid
+  // preconditioner of the finer levels' Schur-complement solves)
+  if (o->smoother == BMG_BSR_EXACT && h->levels.size() >= 3 &&
+      (rc = bsr_exact_bottom_setup(h->levels[h->levels.size() - 2], h->d_flag, st)))
+    return fail(rc);
   h->fine_op = s->fine;
   h->fine_op.owns_coefs = false;
   if ((rc = tune_hierarchy(h, st))) return fail(rc);

@@ -155,6 +155,7 @@ struct Level {
   int cg_grid = 0;                     // CTAs of the CG kernels (partials per reduction)
   int *cg_flag = nullptr;              // device [done, iterations]
   double *smg = nullptr;               // multigrid preconditioner of S: b, xa, xb, r, e (5 x 2 blk)
+  double *sdense = nullptr;            // exact BSR, last smoothing level: dense S^{-1} (2 n^2 squared)
   // coarsest level: dense inverse on the free DoFs
   int nfree = 0;
   int *free_idx = nullptr;     // [nfree] vector positions of the free DoFs
@@ -351,6 +352,11 @@ template <typename T>
 int launch_coarse_solve(const Level &L, const T *r, T *z, cudaStream_t st);
 int launch_bsr_setup(Level &L, double omega_J, double c_fs_area, cudaStream_t st);
 int bsr_exact_setup(Level &L, cudaStream_t st);
+int bsr_exact_bottom_setup(Level &L, int *d_flag, cudaStream_t st);
+// dense Gauss-Jordan inversion kernels (coarse.cu), also used for exact BSR's bottom level
+__global__ void gj_pivot_kernel(double *Aug, int N, int k, double *fac, double tol, int *flag);
+__global__ void gj_eliminate_kernel(double *Aug, int N, int k, const double *fac);
+__global__ void extract_inverse_kernel(const double *Aug, int N, double *inv64, float *inv32);
 int launch_bsr_exact_sweep(const Level *levels, int nsmooth, int l, const double *r, double *x, double omega,
                            cudaStream_t st, bool assign, int *iters_max);
 template <typename T>

@@ -743,6 +743,44 @@ __global__ void __launch_bounds__(kCgThreads) s_prolong_kernel(Grid gf, Grid gc,
   }
 }
 
+// P0 index r in [0, 2 n^2) (L cells first, then U, row-major) -> slot of the two-block vector
+__device__ __forceinline__ size_t s_slot(const Grid &g, int r) {
+  const int nn = g.n * g.n, t = r / nn, c = r % nn;
+  return (size_t)t * g.blk + (size_t)(c / g.n) * g.pitch + c % g.n;
+}
+
+// Aug = [S | I] for the dense inversion: column c of S is S applied to the unit vector e_c
+// (one thread per (cell, column)).
+__global__ void s_dense_kernel(const __grid_constant__ SOp o, double *Aug) {
+  const int n = o.g.n, N = 2 * n * n;
+  const int col = blockIdx.y;
+  const size_t sc = s_slot(o.g, col), ld = 2 * (size_t)N;
+  for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < n * n; cc += gridDim.x * blockDim.x) {
+    const int i = cc % n, j = cc / n;
+    double yL, yU, qL, qU;
+    s_product(o.g, o.c, o.dw, o.dinv, i, j, [&](size_t k) { return k == sc ? 1.0 : 0.0; }, yL, yU, qL, qU);
+    Aug[(size_t)cc * ld + col] = qL;
+    Aug[(size_t)(n * n + cc) * ld + col] = qU;
+    Aug[(size_t)cc * ld + N + cc] = 1.0;
+    Aug[(size_t)(n * n + cc) * ld + N + n * n + cc] = 1.0;
+  }
+}
+
+// out = S^{-1} b from the dense inverse, one warp per row
+__global__ void s_dense_solve_kernel(Grid g, const double *__restrict__ inv, const double *b, double *out,
+                                     const int *stop) {
+  if (*(volatile const int *)stop) return;
+  const int N = 2 * g.n * g.n;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += (gridDim.x * blockDim.x) >> 5) {
+    double acc = 0.0;
+    for (int c = lane; c < N; c += 32) acc = fma(inv[(size_t)r * N + c], b[s_slot(g, c)], acc);
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
+    if (lane == 0) out[s_slot(g, r)] = acc;
+  }
+}
+
 static SOp sop_of(const Level &L, const int *stop) {
   SOp o;
   o.g = L.g;
@@ -769,6 +807,12 @@ static int smg_vcycle(const Level *levels, int nsmooth, int l, const double *b, 
   double *xa = L.smg + 1 * v, *xb = L.smg + 2 * v, *r = L.smg + 3 * v;
   const SOp o = sop_of(L, stop);
   const dim3 grid(smg_grid(L)), block(kCgThreads);
+  if (l + 1 >= nsmooth && L.sdense) {       // last level: its factored S
+    s_dense_solve_kernel<<<dim3((2 * L.n * L.n * 32 + kCgThreads - 1) / kCgThreads), block, 0, st>>>(
+        L.g, L.sdense, b, out, stop);
+    BMG_CHECK_LAUNCH("s_dense_solve_kernel");
+    return BMG_OK;
+  }
   if (l + 1 >= nsmooth) {                   // last level: Jacobi steps from zero
     const double *xin = nullptr;
     for (int s = 0; s < kSmgBottom; ++s) {
@@ -798,6 +842,44 @@ static int smg_vcycle(const Level *levels, int nsmooth, int l, const double *b, 
   BMG_CHECK_LAUNCH("s_jacobi_kernel");
   s_jacobi_kernel<<<grid, block, 0, st>>>(o, b, xb, out, kSmgOmega);
   BMG_CHECK_LAUNCH("s_jacobi_kernel");
+  return BMG_OK;
+}
+
+// The dense inverse of S on the last smoothing level (at most kSmgDenseMax unknowns; larger
+// levels keep the Jacobi bottom): S assembled column by column from the stencil and inverted
+// by Gauss-Jordan with partial pivoting (the coarsest-grid kernels).
+constexpr int kSmgDenseMax = 2048;
+
+int bsr_exact_bottom_setup(Level &L, int *d_flag, cudaStream_t st) {
+  const int N = 2 * L.n * L.n;
+  if (N > kSmgDenseMax) return BMG_OK;
+  int zero = 0;
+  int *nostop = nullptr;
+  double *Aug = nullptr, *fac = nullptr;
+  float *inv32 = nullptr;
+  BMG_CUDA(cudaMalloc(&nostop, sizeof(int)));
+  BMG_CUDA(cudaMemcpyAsync(nostop, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
+  BMG_CUDA(cudaMalloc(&Aug, sizeof(double) * 2 * (size_t)N * N));
+  BMG_CUDA(cudaMemsetAsync(Aug, 0, sizeof(double) * 2 * (size_t)N * N, st));
+  BMG_CUDA(cudaMalloc(&fac, sizeof(double) * N));
+  BMG_CUDA(cudaMalloc(&inv32, sizeof(float) * (size_t)N * N));
+  BMG_CUDA(cudaMalloc(&L.sdense, sizeof(double) * (size_t)N * N));
+  const SOp o = sop_of(L, nostop);
+  s_dense_kernel<<<dim3((L.n * L.n + 127) / 128, N), 128, 0, st>>>(o, Aug);
+  BMG_CHECK_LAUNCH("s_dense_kernel");
+  for (int k = 0; k < N; ++k) {
+    gj_pivot_kernel<<<1, 1024, 0, st>>>(Aug, N, k, fac, 1e-300, d_flag);
+    gj_eliminate_kernel<<<dim3((2 * N + 255) / 256, N), 256, 0, st>>>(Aug, N, k, fac);
+  }
+  g_launches += 2 * (long long)N - 1;
+  BMG_CHECK_LAUNCH("gauss_jordan");
+  extract_inverse_kernel<<<dim3((N + 255) / 256, N), 256, 0, st>>>(Aug, N, L.sdense, inv32);
+  BMG_CHECK_LAUNCH("extract_inverse_kernel");
+  BMG_CUDA(cudaStreamSynchronize(st));
+  cudaFree(Aug);
+  cudaFree(fac);
+  cudaFree(inv32);
+  cudaFree(nostop);
   return BMG_OK;
 }
 
