@@ -559,6 +559,7 @@ def mixed_workload(n, steps, warmup):
            "peak_gbs": peak_gbs, "peak_source": peak_src}
     vin, vout = b.clone(), torch.empty_like(b)
     for key, hp, fam, f64 in (("apply", h["fp32"], "apply", False), ("vanka", h["fp32"], "vanka", False),
+                              ("restrict", h["fp32"], "restrict", False), ("prolong", h["fp32"], "prolong", False),
                               ("vanka_fp64_factors", h["fp32_patch_fp64"], "vanka", True)):
         hp.vcycle(vin, vout)
         torch.cuda.synchronize()

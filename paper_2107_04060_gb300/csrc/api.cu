@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -414,8 +415,67 @@ static int pick_tile(int *slot, int first, int last, F &&launch, cudaEvent_t e0,
   return BMG_OK;
 }
 
+// Tiles chosen by timing are kept per device and level shape for the rest of the process: a
+// later hierarchy with a level of the same shape (grid size, precision, smoother family,
+// coefficient storage, patch-solve precision, whether the TMA operator variant exists) takes
+// the earlier choice without timing again.  Setups that rebuild the same hierarchy many
+// times (one per gradient of a parameter study) then pay for the timing once.
+struct TileKey {
+  int dev, n, kind;            // kind: 0 = V-cycle level, 1 = the FP64 FGMRES operator
+  int fp32, smoother, uniform, klein, wm_full, dense, solve64, tma;
+  bool operator<(const TileKey &o) const {
+    const int a[11] = {dev, n, kind, fp32, smoother, uniform, klein, wm_full, dense, solve64, tma};
+    const int b[11] = {o.dev, o.n, o.kind, o.fp32, o.smoother, o.uniform, o.klein, o.wm_full, o.dense, o.solve64, o.tma};
+    return std::lexicographical_compare(a, a + 11, b, b + 11);
+  }
+};
+struct TileChoice { int apply, vanka, vanka_u; };
+static std::mutex g_tile_mutex;
+static std::map<TileKey, TileChoice> g_tile_cache;
+
+static TileKey tile_key(const bmg_hierarchy *h, const Level &L, int kind) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int fam = h->opts.smoother == BMG_VANKA ? 0 : 1;
+  return TileKey{dev, L.n, kind, kind == 0 && h->opts.precision == BMG_FP32, kind == 0 ? fam : 0,
+                 L.uniform, L.klein, L.wm_full, L.dense_a, L.solve64, kind == 0 && L.tma != nullptr};
+}
+
+static bool tile_cached(const TileKey &k, TileChoice *c) {
+  std::lock_guard<std::mutex> lk(g_tile_mutex);
+  auto it = g_tile_cache.find(k);
+  if (it == g_tile_cache.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+static void tile_store(const TileKey &k, const TileChoice &c) {
+  std::lock_guard<std::mutex> lk(g_tile_mutex);
+  g_tile_cache[k] = c;
+}
+
+template <typename T>
+static int tune_level_timed(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st);
+
 template <typename T>
 static int tune_level(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
+  const char *fa = std::getenv("BMG_FORCE_APPLY_TILE"), *fs = std::getenv("BMG_FORCE_SMOOTHER_TILE");
+  const bool forced = (fa && *fa) || (fs && *fs);
+  const TileKey key = tile_key(h, L, 0);
+  TileChoice c;
+  if (!forced && tile_cached(key, &c)) {
+    L.tile_apply = c.apply;
+    L.tile_vanka = c.vanka;
+    L.tile_vanka_u = c.vanka_u;
+    return BMG_OK;
+  }
+  int rc = tune_level_timed<T>(h, L, e0, e1, st);
+  if (!rc && !forced) tile_store(key, TileChoice{L.tile_apply, L.tile_vanka, L.tile_vanka_u});
+  return rc;
+}
+
+template <typename T>
+static int tune_level_timed(bmg_hierarchy *h, Level &L, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st) {
   T *z = (T *)L.z, *t = (T *)L.t;
   const T *r = (const T *)L.rhs;
   // candidates 0-4: tile shapes; 5 (FP32): 32 x 8 with the input staged by TMA.  The
@@ -451,7 +511,11 @@ static int tune_hierarchy(bmg_hierarchy *h, cudaStream_t st) {
   for (size_t l = 0; l + 1 < h->levels.size() && !rc; ++l)
     rc = fp32 ? tune_level<float>(h, h->levels[l], e0, e1, st) : tune_level<double>(h, h->levels[l], e0, e1, st);
   // the FP64 fine-level operator of FGMRES (its own FP64 scratch vectors)
-  if (!rc) {
+  TileChoice fc;
+  const TileKey fkey = tile_key(h, h->fine_op, 1);
+  if (!rc && tile_cached(fkey, &fc)) {
+    h->fine_op.tile_apply = fc.apply;
+  } else if (!rc) {
     Level &F = h->fine_op;
     const size_t vl = vec_len_of(F.n);
     double *a = nullptr, *b = nullptr;
@@ -461,6 +525,7 @@ static int tune_hierarchy(bmg_hierarchy *h, cudaStream_t st) {
       cudaMemsetAsync(a, 0, sizeof(double) * vl, st);
       rc = pick_tile(&F.tile_apply, 0, 9, [&] { return launch_apply<double>(F, a, a, b, true, 1, 0, st); },
                      e0, e1, st);
+      if (!rc) tile_store(fkey, TileChoice{F.tile_apply, -1, -1});
     }
     cudaStreamSynchronize(st);
     cudaFree(a);
