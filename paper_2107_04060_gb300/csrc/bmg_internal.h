@@ -95,7 +95,7 @@ void galerkin_coarsen_coefs(const OpCoefs<double> &fine, OpCoefs<double> *c64, O
 //   restriction:  coarse value (type t) at (I, J) = sum_k coef_k * fine[ftype_k][2J + dj_k][2I + di_k]
 struct StencilEntry {
   int8_t type, di, dj, pad;
-  float pad2;
+  float coef32;                // coef rounded to FP32 (the FP32 transfers' operand)
   double coef;
 };
 constexpr int kMaxPro = 24;   // entries per (fine type, parity)

@@ -458,6 +458,7 @@ void build_transfer_tables(TransferTables *t) {
           e.di = (int8_t)(kv.first.i - C0);
           e.dj = (int8_t)(kv.first.j - C0);
           e.coef = kv.second;
+          e.coef32 = (float)kv.second;
         }
       t->npro[ty][par] = k;
     }
@@ -473,6 +474,7 @@ void build_transfer_tables(TransferTables *t) {
       e.di = (int8_t)(row.first.i - 2 * C0);
       e.dj = (int8_t)(row.first.j - 2 * C0);
       e.coef = it->second;
+      e.coef32 = (float)it->second;
     }
     t->nres[ct] = k;
   }

@@ -27,6 +27,48 @@ int upload_transfer_tables() {
   return BMG_OK;
 }
 
+// The coefficient of an entry in the transfer's precision (FP32: the table's rounded copy,
+// so no conversion instruction runs on the FP64 pipe).
+template <typename T>
+__device__ __forceinline__ T stencil_coef(const StencilEntry &se) {
+  if constexpr (sizeof(T) == 4) return se.coef32;
+  else return se.coef;
+}
+
+// FP32 transfers: sum over the n entries of a stencil table of coef * src[type plane][row]
+// [col], the entries taken in groups of 8 whose loads are all issued before any of them is
+// used (positions outside the grid load nothing and add coef * 0), so each thread has 8
+// loads in flight instead of one; the additions keep the table's order.  (The FP64
+// transfers keep the plain loop: there the grouping cost more than it saved, 33 against
+// 31 us and 55 against 39 us at 512^2.)  entry(e) reads entry e of the table
+// (constant memory); pos(se, col, row) gives the grid position of an entry and whether it
+// lies inside the grid.
+template <typename T, typename S, typename Get, typename Pos>
+__device__ __forceinline__ S stencil_sum(Get &&entry, int n, const T *__restrict__ src, size_t blk, int pitch,
+                                         Pos &&pos) {
+  S acc = 0;
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    S v[8], c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = S(0);
+      c[k] = S(0);
+      if (e0 + k < n) {
+        const StencilEntry &se = entry(e0 + k);
+        int col, row;
+        if (pos(se, col, row)) {
+          v[k] = (S)__ldg(src + se.type * blk + (size_t)row * pitch + col);
+          c[k] = stencil_coef<S>(se);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (e0 + k < n) acc += c[k] * v[k];
+  }
+  return acc;
+}
+
 // One thread per (coarse position, DoF type): blockIdx.z is the type.
 template <typename T>
 __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *__restrict__ rc,
@@ -44,12 +86,21 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
     bool m[NBLK];
     dof_masks(I, J, nc, m);
     if (m[ct]) {
-      const int ne = c_nres[ct];
-      for (int e = 0; e < ne; ++e) {
-        const StencilEntry se = c_res[ct][e];
-        const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
-        if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
-        acc += (T)se.coef * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
+      if constexpr (sizeof(T) == 4) {
+        acc = stencil_sum<T, T>([&](int e) -> const StencilEntry & { return c_res[ct][e]; }, c_nres[ct], rf,
+                                gf.blk, gf.pitch, [&](const StencilEntry &se, int &fi, int &fj) {
+                                  fi = 2 * I + se.di;
+                                  fj = 2 * J + se.dj;
+                                  return fi >= 0 && fj >= 0 && fi <= nf && fj <= nf;
+                                });
+      } else {
+        const int ne = c_nres[ct];
+        for (int e = 0; e < ne; ++e) {
+          const StencilEntry se = c_res[ct][e];
+          const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
+          if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
+          acc += (T)se.coef * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
+        }
       }
     }
   }
@@ -76,12 +127,21 @@ __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__
   const int I0 = i >> 1, J0 = j >> 1;
   const size_t o = (size_t)j * gf.pitch + i;
   T acc = 0;
-  const int ne = c_npro[t][par];
-  for (int e = 0; e < ne; ++e) {
-    const StencilEntry se = c_pro[t][par][e];
-    const int I = I0 + se.di, J = J0 + se.dj;
-    if (I < 0 || J < 0 || I > nc || J > nc) continue;
-    acc += (T)se.coef * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
+  if constexpr (sizeof(T) == 4) {
+    acc = stencil_sum<T, T>([&](int e) -> const StencilEntry & { return c_pro[t][par][e]; }, c_npro[t][par], xc,
+                            gc.blk, gc.pitch, [&](const StencilEntry &se, int &I, int &J) {
+                              I = I0 + se.di;
+                              J = J0 + se.dj;
+                              return I >= 0 && J >= 0 && I <= nc && J <= nc;
+                            });
+  } else {
+    const int ne = c_npro[t][par];
+    for (int e = 0; e < ne; ++e) {
+      const StencilEntry se = c_pro[t][par][e];
+      const int I = I0 + se.di, J = J0 + se.dj;
+      if (I < 0 || J < 0 || I > nc || J > nc) continue;
+      acc += (T)se.coef * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
+    }
   }
   xf[t * gf.blk + o] += acc;
 }
