@@ -27,46 +27,23 @@ int upload_transfer_tables() {
   return BMG_OK;
 }
 
-// The coefficient of an entry in the transfer's precision (FP32: the table's rounded copy,
-// so no conversion instruction runs on the FP64 pipe).
-template <typename T>
-__device__ __forceinline__ T stencil_coef(const StencilEntry &se) {
-  if constexpr (sizeof(T) == 4) return se.coef32;
-  else return se.coef;
-}
+// FP32 stencil tables staged in shared memory by each CTA: the flat offset of every entry
+// (type plane, row and column folded for this level's layout) and its FP32 coefficient, with
+// the largest row/column reach of the table.  Positions whose whole stencil lies inside the
+// grid then cost one shared read, one load and one multiply-add per entry, with no bounds
+// test; the others take the checked path.  The sums keep the table's order.  (The FP32
+// transfers are bound by instruction issue; the FP64 ones keep the plain per-entry loop.)
+template <int N>
+struct StagedStencil {
+  long long off[N];
+  float coef[N];
+  int n, reach;
+};
 
-// FP32 transfers: sum over the n entries of a stencil table of coef * src[type plane][row]
-// [col], the entries taken in groups of 8 whose loads are all issued before any of them is
-// used (positions outside the grid load nothing and add coef * 0), so each thread has 8
-// loads in flight instead of one; the additions keep the table's order.  (The FP64
-// transfers keep the plain loop: there the grouping cost more than it saved, 33 against
-// 31 us and 55 against 39 us at 512^2.)  entry(e) reads entry e of the table
-// (constant memory); pos(se, col, row) gives the grid position of an entry and whether it
-// lies inside the grid.
-template <typename T, typename S, typename Get, typename Pos>
-__device__ __forceinline__ S stencil_sum(Get &&entry, int n, const T *__restrict__ src, size_t blk, int pitch,
-                                         Pos &&pos) {
-  S acc = 0;
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    S v[8], c[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      v[k] = S(0);
-      c[k] = S(0);
-      if (e0 + k < n) {
-        const StencilEntry &se = entry(e0 + k);
-        int col, row;
-        if (pos(se, col, row)) {
-          v[k] = (S)__ldg(src + se.type * blk + (size_t)row * pitch + col);
-          c[k] = stencil_coef<S>(se);
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (e0 + k < n) acc += c[k] * v[k];
-  }
-  return acc;
+__device__ __forceinline__ void stage_stencil_entry(const StencilEntry &se, size_t blk, int pitch,
+                                                    long long &off, float &coef) {
+  off = (long long)se.type * (long long)blk + (long long)se.dj * pitch + se.di;
+  coef = se.coef32;
 }
 
 // One thread per (coarse position, DoF type): blockIdx.z is the type.
@@ -79,6 +56,43 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int ct = blockIdx.z;
   const int nc = gc.n, nf = gf.n;
+  if constexpr (sizeof(T) == 4) {
+    __shared__ StagedStencil<kMaxRes> st;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const int ne = c_nres[ct];
+    for (int e = tid; e < ne; e += nt) stage_stencil_entry(c_res[ct][e], gf.blk, gf.pitch, st.off[e], st.coef[e]);
+    if (tid == 0) {
+      int r = 0;
+      for (int e = 0; e < ne; ++e) r = max(r, max(abs((int)c_res[ct][e].di), abs((int)c_res[ct][e].dj)));
+      st.n = ne;
+      st.reach = r;
+    }
+    __syncthreads();
+    if (I >= gc.pitch || J > nc) return;
+    const size_t o = (size_t)J * gc.pitch + I;
+    float acc = 0.f;
+    if (I <= nc) {
+      bool m[NBLK];
+      dof_masks(I, J, nc, m);
+      if (m[ct]) {
+        const int rch = st.reach, fi0 = 2 * I, fj0 = 2 * J;
+        if (fi0 - rch >= 0 && fj0 - rch >= 0 && fi0 + rch <= nf && fj0 + rch <= nf) {
+          const float *base = rf + (size_t)fj0 * gf.pitch + fi0;
+#pragma unroll 4
+          for (int e = 0; e < ne; ++e) acc += st.coef[e] * __ldg(base + st.off[e]);
+        } else {
+          for (int e = 0; e < ne; ++e) {
+            const StencilEntry se = c_res[ct][e];
+            const int fi = fi0 + se.di, fj = fj0 + se.dj;
+            if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
+            acc += se.coef32 * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
+          }
+        }
+      }
+    }
+    rc[ct * gc.blk + o] = acc;
+    return;
+  }
   if (I >= gc.pitch || J > nc) return;
   const size_t o = (size_t)J * gc.pitch + I;
   T acc = 0;
@@ -86,21 +100,12 @@ __global__ void restrict_kernel(Grid gf, Grid gc, const T *__restrict__ rf, T *_
     bool m[NBLK];
     dof_masks(I, J, nc, m);
     if (m[ct]) {
-      if constexpr (sizeof(T) == 4) {
-        acc = stencil_sum<T, T>([&](int e) -> const StencilEntry & { return c_res[ct][e]; }, c_nres[ct], rf,
-                                gf.blk, gf.pitch, [&](const StencilEntry &se, int &fi, int &fj) {
-                                  fi = 2 * I + se.di;
-                                  fj = 2 * J + se.dj;
-                                  return fi >= 0 && fj >= 0 && fi <= nf && fj <= nf;
-                                });
-      } else {
-        const int ne = c_nres[ct];
-        for (int e = 0; e < ne; ++e) {
-          const StencilEntry se = c_res[ct][e];
-          const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
-          if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
-          acc += (T)se.coef * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
-        }
+      const int ne = c_nres[ct];
+      for (int e = 0; e < ne; ++e) {
+        const StencilEntry se = c_res[ct][e];
+        const int fi = 2 * I + se.di, fj = 2 * J + se.dj;
+        if (fi < 0 || fj < 0 || fi > nf || fj > nf) continue;
+        acc += (T)se.coef * __ldg(rf + se.type * gf.blk + (size_t)fj * gf.pitch + fi);
       }
     }
   }
@@ -119,6 +124,41 @@ __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__
   const int j = 2 * blockIdx.y + (threadIdx.y >> 1);
   const int t = blockIdx.z;
   const int nf = gf.n, nc = gc.n;
+  if constexpr (sizeof(T) == 4) {
+    // the four parity classes' tables (threadIdx.y is the class), staged as in restrict_kernel
+    __shared__ StagedStencil<kMaxPro> st[4];
+    const int cls = threadIdx.y, ne = c_npro[t][cls];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x)
+      stage_stencil_entry(c_pro[t][cls][e], gc.blk, gc.pitch, st[cls].off[e], st[cls].coef[e]);
+    if (threadIdx.x == 0) {
+      int r = 0;
+      for (int e = 0; e < ne; ++e) r = max(r, max(abs((int)c_pro[t][cls][e].di), abs((int)c_pro[t][cls][e].dj)));
+      st[cls].n = ne;
+      st[cls].reach = r;
+    }
+    __syncthreads();
+    if (i > nf || j > nf) return;
+    bool mk[NBLK];
+    dof_masks(i, j, nf, mk);
+    if (!mk[t]) return;
+    const int I0 = i >> 1, J0 = j >> 1, rch = st[cls].reach;
+    const size_t o = (size_t)j * gf.pitch + i;
+    float acc = 0.f;
+    if (I0 - rch >= 0 && J0 - rch >= 0 && I0 + rch <= nc && J0 + rch <= nc) {
+      const float *base = xc + (size_t)J0 * gc.pitch + I0;
+#pragma unroll 4
+      for (int e = 0; e < ne; ++e) acc += st[cls].coef[e] * __ldg(base + st[cls].off[e]);
+    } else {
+      for (int e = 0; e < ne; ++e) {
+        const StencilEntry se = c_pro[t][cls][e];
+        const int I = I0 + se.di, J = J0 + se.dj;
+        if (I < 0 || J < 0 || I > nc || J > nc) continue;
+        acc += se.coef32 * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
+      }
+    }
+    xf[t * gf.blk + o] += acc;
+    return;
+  }
   if (i > nf || j > nf) return;
   bool m[NBLK];
   dof_masks(i, j, nf, m);
@@ -127,21 +167,12 @@ __global__ void prolong_kernel(Grid gf, Grid gc, const T *__restrict__ xc, T *__
   const int I0 = i >> 1, J0 = j >> 1;
   const size_t o = (size_t)j * gf.pitch + i;
   T acc = 0;
-  if constexpr (sizeof(T) == 4) {
-    acc = stencil_sum<T, T>([&](int e) -> const StencilEntry & { return c_pro[t][par][e]; }, c_npro[t][par], xc,
-                            gc.blk, gc.pitch, [&](const StencilEntry &se, int &I, int &J) {
-                              I = I0 + se.di;
-                              J = J0 + se.dj;
-                              return I >= 0 && J >= 0 && I <= nc && J <= nc;
-                            });
-  } else {
-    const int ne = c_npro[t][par];
-    for (int e = 0; e < ne; ++e) {
-      const StencilEntry se = c_pro[t][par][e];
-      const int I = I0 + se.di, J = J0 + se.dj;
-      if (I < 0 || J < 0 || I > nc || J > nc) continue;
-      acc += (T)se.coef * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
-    }
+  const int ne = c_npro[t][par];
+  for (int e = 0; e < ne; ++e) {
+    const StencilEntry se = c_pro[t][par][e];
+    const int I = I0 + se.di, J = J0 + se.dj;
+    if (I < 0 || J < 0 || I > nc || J > nc) continue;
+    acc += (T)se.coef * __ldg(xc + se.type * gc.blk + (size_t)J * gc.pitch + I);
   }
   xf[t * gf.blk + o] += acc;
 }
