@@ -20,6 +20,16 @@ Every routine follows the paper's definitions step by step, in numpy / scipy wit
                Eq. TG-Operator-Biot; Sec. 5.1), two-grid measured factor rho_N (Sec. 4.3)
   krylov.py    right-preconditioned flexible GMRES (Sec. 5.1)
   manufactured.py  loads and errors for the steady manufactured problem (Sec. 5.1)
+  timedep.py   backward-Euler time stepping on a smooth manufactured solution (Sec. 2.1,
+               Eqs. discrete1-3)
+  lfa.py       two-grid local Fourier analysis (Sec. 4, App. A-D): Vanka, inexact and exact
+               BSR, rediscretised or Galerkin coarse symbols
+  omega_table.py  the bench's damping by brute-force LFA minimisation (Sec. 4.3), written to
+               tests/golden/omega_lfa.json
+  adjoint.py   gradients of a pressure misfit through direct solves (checked by central
+               differences)
+mg.py also holds W-cycles (gamma = 2) and Galerkin coarse operators; smoothers.py exact BSR
+(the pressure step of Eq. bsr_p solved with a sparse LU of S).
 
 Parity status of each function is stated in its docstring ("pinned by ..." or
 "parity unpinned").

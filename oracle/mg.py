@@ -10,8 +10,15 @@ One V(nu1, nu2) cycle for A_l x = b_l from x = 0:
     nu1 relaxations; r = b - A x; x_c = V-cycle(R r) (or the direct solve on the coarsest
     level); x <- x + P x_c; nu2 relaxations.
 
+W-cycles (gamma = 2): the coarse problem of each level approximated by two cycles, the
+second on the residual the first leaves.  Galerkin coarse operators (coarse_op="galerkin"):
+R A P on every level.
+
 Pinned by: Table 2 / Table 3 two-grid factors and Table 4 iteration counts
-(tests/test_oracle_mg.py); direct-solve parity through FGMRES (tests/test_oracle_mg.py).
+(tests/test_oracle_mg.py); direct-solve parity through FGMRES (tests/test_oracle_mg.py); the
+W-cycle by the two-grid factor and the LFA prediction it restores for multilevel inexact BSR;
+Galerkin coarse operators by the nested-space identities (tests/test_oracle_mg.py,
+tests/test_oracle_lfa.py).
 """
 from __future__ import annotations
 

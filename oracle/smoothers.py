@@ -18,9 +18,14 @@ with y = (u, w):
     x    <- x + omega (dy, dp)
 The inner Vanka is undamped with natural weights.
 
+Exact Braess-Sarazin (Sec. 3.2.2, ``exact=True``): the same steps with Eq. bsr_p solved,
+dp = S^{-1} (B z - r_p), by a sparse LU of S.
+
 Pinned by: the measured two-grid factors of Tables 2 and 3 (tests/test_oracle_mg.py); the
 patch regularisation for 1/M = 0 by the identity "shifted patches at 1/M = 0 equal the
-unshifted patches at 1/M = s" (tests/test_oracle_mg.py).
+unshifted patches at 1/M = s" (tests/test_oracle_mg.py); exact BSR by both block equations
+of its correction with S written out from its definition, and through the LFA by the
+paper's exact-BSR remarks (tests/test_oracle_mg.py, tests/test_oracle_lfa.py).
 """
 from __future__ import annotations
 
